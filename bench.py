@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the LVQ search hot path on B300.
+
+Workload (default): multi-means LVQ-4x8, 10,000,000 vectors of d = 768 drawn
+from a 256-component Gaussian mixture (sigma 0.3, unit-normalised), 16
+centring means fitted by k-means on a 100k sample, inner product.  One step
+is one pass of the whole hot path over one batch of synthetic input:
+
+  1. lvq_delete of 10,000 live slots and lvq_insert of 10,000 new vectors
+     (mean assignment, centring, bounds, both code levels, slot reuse);
+  2. lvq_search_exhaustive of a mix of uneven query batches (sizes {1, 4096}
+     and 30 log-uniform draws in [1, 4096], concatenated into one launch),
+     top-100 on the first level, re-ranked to top-10 with the residuals;
+  3. lvq_search_candidates of 1,024 queries x 2,048 candidate ids (70% from
+     the query's own component), top-50 re-ranked to top-10.
+
+``value`` is first-level (query, vector) distances per second over the
+whole step with inputs resident in HBM; ``e2e`` is the same through the C
+ABI with the step's inputs copied from pinned host memory and its results
+copied back inside the timed region.  The compressed database (3.9 GB of
+codes) is larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "mlvq4x8-ip-10m-d768"
+METRIC = "LVQ-4x8 distances/s & QPS@recall10 at 10M x 768"
+UNIT = "distances/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="database size (default: the workload's)")
+    ap.add_argument("--mix", default="full", choices=["full", "small"],
+                    help="query mix: full = {1,4096} + 30 log-uniform in [1,4096]; small = 8 in [1,256]")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def query_mix(kind: str, seed: int):
+    if kind == "small":
+        return synth.log_uniform_sizes(8, 1, 256, seed)
+    return np.concatenate([[1, 4096], synth.log_uniform_sizes(30, 1, 4096, seed)])
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons (200 ms)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(units: float, seconds: float, world: int):
+    """Whole-job units and the slowest rank's time (max over ranks)."""
+    if world == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([units, seconds], dtype=torch.float64, device=dev)
+    u = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+# --------------------------------------------------------------------------
+
+def cpu_baseline(mix, means, q_host, sample_rows=40_000, sample_queries=8, k1=100, k=10):
+    import oracle as O
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    x = mix.rows(0, sample_rows)
+    enc = O.encode(x, means, 4, 8)
+    q = q_host[:sample_queries]
+    t0 = time.perf_counter()
+    O.search_exhaustive(enc, means, q, k1, k, O.IP)
+    dt = time.perf_counter() - t0
+    return {"value": sample_rows * sample_queries / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle brute-force search (first level over {sample_rows} rows of the workload, "
+                      f"top-{k1}, two-level re-rank to top-{k}) for {sample_queries} queries; "
+                      f"{dt:.2f} s; float64 decode + numpy/OpenBLAS"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, same metric."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    w = synth.WORKLOADS[WORKLOAD]
+    mix = synth.mixture_for(WORKLOAD)
+    means = synth.kmeans_means(mix.rows(0, 20_000, stream=5), w["n_means"], seed=3003, iters=10)
+    q = mix.queries(16)
+    times = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(mix, means, q, sample_rows=20_000, sample_queries=4)
+        if i >= args.warmup:
+            times.append(r)
+        base = r
+    vals = [r["value"] for r in times] or [base["value"]]
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w["n"], "d": w["d"], "n_means": w["n_means"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_setup()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2402_02044_b300 import build
+    build.build()
+    from paper_2402_02044_b300 import Store
+    from paper_2402_02044_b300 import lvq as L
+
+    w = synth.WORKLOADS[WORKLOAD]
+    n = args.n or w["n"]
+    d = w["d"]
+    mix = synth.mixture_for(WORKLOAD)
+    t_setup = time.time()
+    sample = mix.rows(0, min(w["kmeans_sample"], n), stream=5)
+    means = synth.kmeans_means(sample, w["n_means"], seed=3003, iters=25)
+    B_upd = 10_000
+    steps_total = args.warmup + 2 * args.steps
+    st = Store(d, 4, 8, means, "ip", n)
+    chunk = 1 << 20
+    for s in range(0, n, chunk):
+        xs = torch.from_numpy(mix.rows(s, min(n, s + chunk))).cuda()
+        st.insert(xs)
+    torch.cuda.synchronize()
+    assert st.stats() == n
+    # queries
+    sizes = query_mix(args.mix, 4003)
+    nq = int(sizes.sum())
+    q_host = mix.queries(nq)
+    q_dev = torch.from_numpy(q_host).cuda()
+    # ID-gather batch
+    nq_g, C = 1024, 2048
+    lab_db = mix.labels(0, n)
+    qg_host, qg_lab = mix.rows(0, nq_g, stream=3, with_labels=True)
+    cand_host = synth.candidate_lists(lab_db, qg_lab, C, 0.7, seed=4004)
+    qg_dev = torch.from_numpy(qg_host).cuda()
+    cand_dev = torch.from_numpy(cand_host).cuda()
+    # per-step update batches: delete initially filled slots, insert fresh vectors
+    g = np.random.default_rng(7000 + rank)
+    del_host = [np.sort(g.choice(n, B_upd, replace=False)).astype(np.int64) for _ in range(steps_total)]
+    # keep the delete sets disjoint from each other's re-inserted slots: draw
+    # every step's ids from slots that are still original
+    used = set()
+    for i in range(steps_total):
+        s_ = [v for v in del_host[i].tolist() if v not in used]
+        while len(s_) < B_upd:
+            extra = int(g.integers(0, n))
+            if extra not in used and extra not in s_:
+                s_.append(extra)
+        del_host[i] = np.array(sorted(s_), dtype=np.int64)
+        used.update(s_)
+    ins_host = [mix.rows(i * B_upd, (i + 1) * B_upd, stream=7) for i in range(steps_total)]
+    del_dev = [torch.from_numpy(a).cuda() for a in del_host]
+    ins_dev = [torch.from_numpy(a).cuda() for a in ins_host]
+    precision = args.precision
+    st.reserve(nq, 100, C)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
+
+    def step(i, qd, qgd, cd, dd, xd):
+        st.delete(dd)
+        st.insert(xd)
+        ids, sc = st.search(qd, 10, 100, precision)
+        gi, gs = st.search_candidates(qgd, cd, 10, 50)
+        return ids, sc, gi, gs
+
+    for i in range(args.warmup):
+        step(i, q_dev, qg_dev, cand_dev, del_dev[i], ins_dev[i])
+    torch.cuda.synchronize()
+
+    # timed region (device-resident inputs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.lvq_profile_enable(st.handle, True)
+    L.lvq_profile_read(st.handle)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(args.steps):
+        j = args.warmup + i
+        step(j, q_dev, qg_dev, cand_dev, del_dev[j], ins_dev[j])
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = L.lvq_profile_read(st.handle)
+    L.lvq_profile_enable(st.handle, False)
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    n_live = st.stats()
+    dist_per_step = nq * n_live + nq_g * C
+    units, t_max = aggregate(dist_per_step * args.steps, t_dev, world)
+    value = units / t_max
+    qps = (nq + nq_g) * args.steps * world / t_max
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        q_pin, qg_pin, cand_pin = pin(q_host), pin(qg_host), pin(cand_host)
+        del_pin = [pin(a) for a in del_host]
+        ins_pin = [pin(a) for a in ins_host]
+        out_pin = [torch.empty((nq, 10), dtype=torch.int64).pin_memory(),
+                   torch.empty((nq, 10), dtype=torch.float32).pin_memory(),
+                   torch.empty((nq_g, 10), dtype=torch.int64).pin_memory(),
+                   torch.empty((nq_g, 10), dtype=torch.float32).pin_memory()]
+        h2d = q_host.nbytes + qg_host.nbytes + cand_host.nbytes + del_host[0].nbytes + ins_host[0].nbytes
+        d2h = sum(t.numel() * t.element_size() for t in out_pin)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            j = args.warmup + args.steps + i
+            qd = q_pin.cuda(non_blocking=True)
+            qgd = qg_pin.cuda(non_blocking=True)
+            cd = cand_pin.cuda(non_blocking=True)
+            dd = del_pin[j].cuda(non_blocking=True)
+            xd = ins_pin[j].cuda(non_blocking=True)
+            res = step(j, qd, qgd, cd, dd, xd)
+            for o, r in zip(out_pin, res):
+                o.copy_(r, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        t_e2e = e0.elapsed_time(e1) / 1e3
+        u2, t2 = aggregate(dist_per_step * args.steps, t_e2e, world)
+        e2e = {"value": u2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant kernel
+    scan_kind = "scan_mma" if prof["scan_mma"][1] else "scan_fp32"
+    scan_ms, scan_launches = prof[scan_kind]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    flops_per_launch = 2.0 * nq * n_live * d
+    bytes_per_launch = n_live * (384 + 8 + 1)
+    per_launch_s = scan_ms / 1e3 / max(scan_launches, 1)
+    if scan_kind == "scan_mma":
+        achieved = flops_per_launch / per_launch_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1400.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops_sustained; fp16 rate = bf16 rate)"
+                if "bf16_tflops_sustained" in peaks else "fallback"}
+    else:
+        achieved = flops_per_launch / per_launch_s / 1e12
+        mhz = clk.get("sm_mhz") or 1900.0
+        peak = 148 * 128 * 2 * mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock"}
+    roof["kernel"] = scan_kind
+    roof["algorithmic_bytes_per_launch"] = bytes_per_launch
+    roof["hbm_gbs_equiv"] = bytes_per_launch / per_launch_s / 1e9
+    launches = sum(c for _, c in prof.values())
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16xf16->f32 (first level), f32 (encode, re-rank)" if scan_kind == "scan_mma" else "f32",
+            "data": "synthetic (seeded Gaussian mixture; stands in for the paper's datasets)",
+            "config": {"workload": WORKLOAD, "n": n, "d": d, "bits": "4x8", "n_means": w["n_means"],
+                       "metric": "ip", "queries_per_step": int(nq), "query_batches": [int(v) for v in sizes],
+                       "k1": 100, "k": 10, "gather_queries": nq_g, "gather_candidates": C,
+                       "updates_per_step": B_upd, "l2_flush": "not needed: 3.9 GB of codes > 126 MB L2",
+                       "precision": precision},
+            "qps": qps, "recall_at_10": None,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
+            "setup_s": t_setup}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mix, means, q_host)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    st.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

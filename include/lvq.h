@@ -1,0 +1,216 @@
+/*
+ * lvq.h -- C ABI of a B300 (sm_103a) library for Locally-adaptive Vector
+ * Quantization search (Aguerrebere et al., "Locally-Adaptive Quantization for
+ * Streaming Vector Search", arxiv 2402.02044).
+ *
+ * The library keeps LVQ-compressed vectors in a device-resident store and
+ * scores batches of float32 queries against them:
+ *   - encoding (Eq. 1-3 and Def. 1): centring by the nearest of M means,
+ *     per-vector lower bound l and step D, B1-bit first-level codes and
+ *     optional B2-bit residual codes on the grid Q_{B2,-D/2,D/2} (Sec. 2.2);
+ *   - first-level scoring of 4-bit or 8-bit codes for the squared Euclidean
+ *     distance or the inner product (Sec. 3.2), exhaustively or restricted to
+ *     a candidate list, fused with top-k1 selection;
+ *   - re-ranking of the k1 candidates with both levels (Sec. 2.2, App. C);
+ *   - inserts into free slots and lazy deletes that are filtered out of
+ *     every result (Sec. 2.1, App. A.2).
+ *
+ * Conventions for every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller unless the
+ *     argument name ends in _host.  The library never frees them.
+ *   - Work is enqueued on the given stream (NULL = legacy default stream) and
+ *     the call returns without waiting for it.  Argument errors are returned
+ *     at once and nothing is enqueued.  Errors found on the device (an id out
+ *     of range, a full store) are recorded in the store and returned by the
+ *     next call that synchronises (lvq_last_error, lvq_stats).
+ *   - Calls that use one store must be ordered (one stream, or events): they
+ *     share the store's scratch memory.
+ *   - No C++ exception crosses this interface.
+ *   - Results are sorted best first: ascending squared distance (LVQ_L2) or
+ *     descending inner product (LVQ_IP); equal scores are ordered by
+ *     ascending id.  A query with fewer than k live results is padded with
+ *     id -1 and score +inf (LVQ_L2) or -inf (LVQ_IP).
+ *   - Ids are slot indices in [0, capacity).
+ */
+#ifndef LVQ_H
+#define LVQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *lvq_stream_t;
+
+typedef enum {
+  LVQ_OK = 0,
+  LVQ_EINVAL = 1,    /* bad argument (null pointer, size or option out of range) */
+  LVQ_ENOMEM = 2,    /* device allocation failed */
+  LVQ_EFULL = 3,     /* an insert needed more free slots than the store had */
+  LVQ_ENOTFOUND = 4, /* lvq_export was given an id that is not live */
+  LVQ_ECUDA = 5,     /* a CUDA call failed (launch error, sticky device fault) */
+  LVQ_ETIMEOUT = 6,  /* a bounded device wait gave up */
+  LVQ_EBUSY = 7      /* reserved */
+} lvq_status;
+
+typedef enum { LVQ_L2 = 0, LVQ_IP = 1 } lvq_metric;
+
+/* Arithmetic of the first-level scan <q, c>:
+ *   LVQ_FP32      plain float32 on CUDA cores;
+ *   LVQ_FP16_MMA  q rounded to float16, codes exact in float16, products
+ *                 accumulated in float32 on the tcgen05 tensor cores;
+ *   LVQ_AUTO      the library's choice for the batch size (tensor cores). */
+typedef enum { LVQ_FP32 = 0, LVQ_FP16_MMA = 1, LVQ_AUTO = 2 } lvq_precision;
+
+typedef struct {
+  int32_t d;        /* dimensionality, 1 .. 4096 */
+  int32_t bits1;    /* first-level bits B1: 4 or 8 */
+  int32_t bits2;    /* residual bits B2: 0 (LVQ-B1) or 8 (LVQ-B1x8) */
+  int32_t n_means;  /* M centring means, 1 .. 256 (M = 1 is plain LVQ) */
+  int32_t metric;   /* lvq_metric */
+  int32_t reserved; /* must be 0 */
+  int64_t capacity; /* number of slots, 1 .. 2^31 - 1 */
+} lvq_config;
+
+typedef struct lvq_store lvq_store; /* opaque; owns all of its device memory */
+
+/* Tile shapes of the scan kernels (chosen by the autotuner).  A field set to
+ * 0 means "library default". */
+typedef struct {
+  int32_t mma_n;      /* queries per tcgen05 tile: 16, 32, 64 or 128 */
+  int32_t mma_splits; /* database splits per query tile (0 = fill the GPU) */
+  int32_t fp32_q;     /* queries per CTA of the float32 scan: 1, 2, 4, 8 or 16 */
+  int32_t fp32_splits;
+} lvq_tuning;
+
+/* Create an empty store on the current CUDA device.
+ * means_host: n_means x d float32 centring means, row-major, HOST memory,
+ *   copied (Sec. 2.2: the sample mean; Def. 1: M centres).
+ * out: receives the store handle.
+ * Errors: LVQ_EINVAL for a bad config, LVQ_ENOMEM, LVQ_ECUDA. */
+lvq_status lvq_create(const lvq_config *cfg, const float *means_host, lvq_store **out);
+
+/* Free the store and all of its device memory.  Synchronises the device. */
+lvq_status lvq_destroy(lvq_store *store);
+
+/* Encode n vectors without touching the store (Eq. 1-3, Def. 1, Sec. 2.2).
+ * x: n x d float32, row-major.
+ * codes1: n x d uint8, one first-level code per byte, in [0, 2^B1 - 1].
+ * codes2: n x d uint8 residual codes in [0, 255], or NULL (required when
+ *   bits2 = 8, ignored when bits2 = 0).
+ * lower, step: n float32 each, l(x) and D of the vector.
+ * mean_id: n uint8, index of the centring mean.
+ * Every float32 step is rounded separately (no fused multiply-add):
+ *   y = x - mu*, l = min y, D = (max y - l)/(2^B1 - 1),
+ *   c = clamp(floor(fl(1/D') * (y - l) + 1/2)), D' = D or 1 when D = 0,
+ *   r = y - (D c + l), c2 likewise with l2 = -D/2, D2 = D/(2^B2 - 1). */
+lvq_status lvq_encode(const lvq_store *store, const float *x, int64_t n, uint8_t *codes1,
+                      uint8_t *codes2, float *lower, float *step, uint8_t *mean_id,
+                      lvq_stream_t stream);
+
+/* Insert n vectors (Sec. 2.1: X_t = X_{t-1} + {x}).  They are encoded on the
+ * device into the n lowest-numbered free slots, in increasing slot order, and
+ * become visible to searches that follow on the stream.
+ * x: n x d float32.  out_ids: n int64, the slots taken.
+ * All or nothing: when fewer than n slots are free nothing is inserted,
+ * out_ids is filled with -1 and LVQ_EFULL is recorded (sticky). */
+lvq_status lvq_insert(lvq_store *store, const float *x, int64_t n, int64_t *out_ids,
+                      lvq_stream_t stream);
+
+/* Delete slots (Sec. 2.1: X_t = X_{t-1} - {x}; lazy, App. A.2): from the
+ * stream position of the call on, the slots are excluded from every result
+ * and are free for later inserts.  Ids that are out of range, already free
+ * or repeated are ignored.
+ * ids: n int64.  out_n_deleted: 1 int64, receives the number freed. */
+lvq_status lvq_delete(lvq_store *store, const int64_t *ids, int64_t n, int64_t *out_n_deleted,
+                      lvq_stream_t stream);
+
+/* Exhaustive search over all live slots (Sec. 3.2 scoring, App. C re-rank).
+ * q: nq x d float32 queries.
+ * k1: first-level candidates per query, 1 .. 512; 0 (or a store without a
+ *   second level) returns the k best first-level results directly.
+ * k: results per query, 1 .. 512 and <= k1 when k1 > 0.
+ * precision: lvq_precision of the first-level scan.
+ * out_ids: nq x k int64; out_scores: nq x k float32.  Scores are the
+ *   two-level distance / inner product when re-ranked, else first level. */
+lvq_status lvq_search_exhaustive(const lvq_store *store, const float *q, int64_t nq, int32_t k1,
+                                 int32_t k, int32_t precision, int64_t *out_ids,
+                                 float *out_scores, lvq_stream_t stream);
+
+/* First stage alone: the k1 best live slots of each query by first-level
+ * score, sorted, with their first-level scores (nq x k1 each). */
+lvq_status lvq_search_first_level(const lvq_store *store, const float *q, int64_t nq, int32_t k1,
+                                  int32_t precision, int64_t *out_ids, float *out_scores,
+                                  lvq_stream_t stream);
+
+/* ID-gather form: the search restricted to each query's candidate list, the
+ * frontier-scoring step of greedy graph search (Alg. 1).  Float32 scoring.
+ * cand: nq x n_cand int64 slot ids; -1, out-of-range, deleted and repeated
+ *   ids are skipped.  n_cand: 1 .. 65536.  k1, k, outputs as in
+ *   lvq_search_exhaustive. */
+lvq_status lvq_search_candidates(const lvq_store *store, const float *q, int64_t nq,
+                                 const int64_t *cand, int32_t n_cand, int32_t k1, int32_t k,
+                                 int64_t *out_ids, float *out_scores, lvq_stream_t stream);
+
+/* Re-rank given candidates with both levels (Sec. 2.2, App. C), float32.
+ * ids: nq x k1 int64 (-1, out-of-range, deleted and repeated ids skipped).
+ * k <= k1 <= 4096.  Outputs nq x k.  Needs a store with bits2 = 8. */
+lvq_status lvq_rerank(const lvq_store *store, const float *q, int64_t nq, const int64_t *ids,
+                      int32_t k1, int32_t k, int64_t *out_ids, float *out_scores,
+                      lvq_stream_t stream);
+
+/* Read stored records back in the lvq_encode layout (one code per byte).
+ * ids: n int64 live slots.  codes2 may be NULL.  A slot that is not live
+ * yields zeros and records LVQ_ENOTFOUND (sticky). */
+lvq_status lvq_export(const lvq_store *store, const int64_t *ids, int64_t n, uint8_t *codes1,
+                      uint8_t *codes2, float *lower, float *step, uint8_t *mean_id,
+                      lvq_stream_t stream);
+
+/* Synchronise the stream, then report the number of live slots (host int64)
+ * and return the first recorded device error (LVQ_OK if none; clears it). */
+lvq_status lvq_stats(const lvq_store *store, int64_t *n_live_host, lvq_stream_t stream);
+
+/* Pre-size the store's scratch memory for calls with up to max_nq queries,
+ * k1 <= max_k1 and n_cand <= max_cand, so that later calls allocate nothing
+ * (needed before capturing them in a CUDA graph). */
+lvq_status lvq_reserve(lvq_store *store, int64_t max_nq, int32_t max_k1, int32_t max_cand);
+
+/* Set / read the scan tile shapes (lvq_tuning). */
+lvq_status lvq_set_tuning(lvq_store *store, const lvq_tuning *tuning);
+lvq_status lvq_get_tuning(const lvq_store *store, lvq_tuning *tuning);
+
+/* Per-kernel timing of the store's own launches, for benchmarks.  While
+ * enabled, every kernel launch of a call on this store is bracketed by CUDA
+ * events recorded on the call's stream.  lvq_profile_read synchronises the
+ * device and returns, per kind (lvq_kernel_kind), the summed elapsed
+ * milliseconds and the launch count since the last read, then resets them.
+ * ms and launches: host arrays of n_kinds entries (n_kinds <= LVQ_KERNEL_KINDS). */
+typedef enum {
+  LVQ_K_PREP = 0,       /* query preparation */
+  LVQ_K_SCAN_FP32 = 1,  /* float32 first-level scan */
+  LVQ_K_SCAN_MMA = 2,   /* tcgen05 first-level scan */
+  LVQ_K_MERGE = 3,      /* per-query merge of split lists (+ re-rank) */
+  LVQ_K_GATHER = 4,     /* ID-gather search */
+  LVQ_K_RERANK = 5,     /* lvq_rerank */
+  LVQ_K_INSERT = 6,     /* slot allocation, encoding, publication */
+  LVQ_K_DELETE = 7,     /* deletes */
+  LVQ_KERNEL_KINDS = 8
+} lvq_kernel_kind;
+lvq_status lvq_profile_enable(lvq_store *store, int32_t on);
+lvq_status lvq_profile_read(lvq_store *store, double *ms, int64_t *launches, int32_t n_kinds);
+
+/* Synchronise the device, copy the last error message (NUL-terminated, at
+ * most len bytes) and return the first recorded error, clearing it. */
+lvq_status lvq_last_error(const lvq_store *store, char *buf, size_t len);
+
+/* Human-readable name of a status code (static storage). */
+const char *lvq_status_string(lvq_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LVQ_H */

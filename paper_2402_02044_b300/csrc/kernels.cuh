@@ -1,0 +1,82 @@
+// Launchers of the LVQ kernels (called by the C ABI in lvq_api.cu).
+#pragma once
+
+#include "lvq_internal.cuh"
+
+namespace lvq {
+
+struct EncodeOut {
+  // plain layout (lvq_encode); unused when slots != nullptr
+  uint8_t* codes1 = nullptr;
+  uint8_t* codes2 = nullptr;
+  float* lower = nullptr;
+  float* step = nullptr;
+  uint8_t* mean_id = nullptr;
+  // store layout (lvq_insert): vector i goes to slot slots[i]
+  const int64_t* slots = nullptr;
+  const int32_t* abort_flag = nullptr;  // set when the insert was abandoned
+};
+
+cudaError_t launch_encode(const DeviceStore& st, const float* x, int64_t n, const EncodeOut& out,
+                          cudaStream_t stream);
+size_t alloc_scratch_bytes(int64_t capacity);
+cudaError_t launch_alloc_slots(const DeviceStore& st, int64_t n, int64_t* out_ids, int32_t* scratch,
+                               int32_t* abort_flag, cudaStream_t stream);
+cudaError_t launch_publish(const DeviceStore& st, const int64_t* ids, int64_t n, const int32_t* abort_flag,
+                           int64_t* n_live, cudaStream_t stream);
+cudaError_t launch_delete(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* out_n,
+                          unsigned long long* count, int64_t* n_live, cudaStream_t stream);
+cudaError_t launch_export(const DeviceStore& st, const int64_t* ids, int64_t n, uint8_t* codes1,
+                          uint8_t* codes2, float* lower, float* step, uint8_t* mean_id, cudaStream_t stream);
+
+// ---- query preparation ------------------------------------------------------
+// Per query: qsum = sum_j q_j, qnorm = ||q||^2, cm[m] = <q, mu_m> (float32),
+// and q rounded to float16 into a zero-padded [nq_pad][kq] matrix.
+struct QueryPrep {
+  float* qsum;      // [nq]
+  float* qnorm;     // [nq]
+  float* cm;        // [nq][M]
+  uint16_t* q16;    // [nq_pad][kq] (may be null)
+  int64_t nq_pad;
+  int kq;
+};
+cudaError_t launch_prep_queries(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                                cudaStream_t stream);
+
+// ---- first-level scans ------------------------------------------------------
+// Both scans write, for every (query, split), the split's k1 best keys in no
+// particular order (kNoKey padded) to partial[(q * splits + split) * k1 + i].
+struct ScanPlan {
+  int splits;           // database splits
+  int64_t n_rows;       // rows scanned: [0, n_rows)
+  int k1;
+  uint64_t* partial;    // [nq][splits][k1]
+  uint64_t* cand;       // per-CTA candidate buffers
+  int grid;             // persistent CTAs
+};
+
+int fp32_scan_grid(const DeviceStore& st, int qb, int sm_count);
+size_t fp32_scan_cand_bytes(int grid, int qb, int k1);
+cudaError_t launch_scan_fp32(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                             int qb, const ScanPlan& plan, cudaStream_t stream);
+
+// tcgen05 scan (scan_mma.cu)
+size_t mma_scan_cand_bytes(int grid, int n_tile, int k1);
+cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& p, int n_tile,
+                            const ScanPlan& plan, cudaStream_t stream);
+bool mma_supported(const DeviceStore& st);
+
+// ---- selection and re-ranking ----------------------------------------------
+// Merge the per-split lists of each query into its k1 best, then either write
+// the k best (first level) or re-rank the k1 with both levels and write k.
+cudaError_t launch_merge_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                                const uint64_t* partial, int splits, int k1, int k, bool rerank,
+                                int64_t* out_ids, float* out_scores, cudaStream_t stream);
+cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                          const int64_t* ids, int k1, int k, int64_t* out_ids, float* out_scores,
+                          cudaStream_t stream);
+cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                          const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
+                          float* out_scores, cudaStream_t stream);
+
+}  // namespace lvq

@@ -1,0 +1,542 @@
+// The C ABI declared in include/lvq.h: argument checks, store memory, scratch
+// sizing and the order of kernel launches of each call.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+#include "topk.cuh"
+
+using namespace lvq;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// counters block layout (device, int64 words)
+enum { kCtrLive = 0, kCtrAbort = 1, kCtrDelCount = 2, kCtrWords = 4 };
+
+lvq_status fail(const lvq_store* s, lvq_status code, const char* msg) {
+  if (s) {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->last_msg = msg;
+  }
+  return code;
+}
+
+lvq_status cuda_fail(const lvq_store* s, cudaError_t e, const char* where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  return fail(s, e == cudaErrorMemoryAllocation ? LVQ_ENOMEM : LVQ_ECUDA, buf);
+}
+
+#define LVQ_CUDA(s, call, where)                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
+  } while (0)
+
+// Scratch memory of one call, carved from the store's workspace.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += (count * sizeof(T) + kAlign - 1) / kAlign * kAlign;
+    return p;
+  }
+};
+
+lvq_status ensure_ws(lvq_store* s, size_t bytes) {
+  if (bytes <= s->ws_bytes) return LVQ_OK;
+  if (s->ws) {
+    cudaError_t e = cudaFree(s->ws);
+    s->ws = nullptr;
+    s->ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaFree(workspace)");
+  }
+  const size_t want = bytes + bytes / 4 + (1 << 20);
+  cudaError_t e = cudaMalloc(&s->ws, want);
+  if (e != cudaSuccess) {
+    s->ws = nullptr;
+    return cuda_fail(s, e, "cudaMalloc(workspace)");
+  }
+  s->ws_bytes = want;
+  return LVQ_OK;
+}
+
+bool valid_stream_device(const lvq_store* s) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == s->device;
+}
+
+int pick_qb(const lvq_store* s, int64_t nq) {
+  if (s->tuning.fp32_q > 0) return s->tuning.fp32_q;
+  if (nq >= 16) return 16;
+  int qb = 1;
+  while (qb < nq) qb <<= 1;
+  return qb;
+}
+
+int pick_mma_n(const lvq_store* s, int64_t nq) {
+  if (s->tuning.mma_n > 0) return s->tuning.mma_n;
+  if (nq <= 16) return 16;
+  if (nq <= 32) return 32;
+  if (nq <= 64) return 64;
+  return 128;
+}
+
+// Layout of the scratch memory of a first-level scan.
+struct ScanScratch {
+  QueryPrep prep;
+  ScanPlan plan;
+  int qb = 0, n_tile = 0;
+  bool mma = false;
+};
+
+size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, ScanScratch* out) {
+  const DeviceStore& st = s->ds;
+  Carver c(base);
+  ScanScratch sc;
+  sc.mma = mma;
+  sc.prep.qsum = c.take<float>(nq);
+  sc.prep.qnorm = c.take<float>(nq);
+  sc.prep.cm = c.take<float>((size_t)nq * st.n_means);
+  sc.prep.q16 = nullptr;
+  sc.prep.nq_pad = nq;
+  sc.prep.kq = 0;
+  const int64_t n_rows = s->rows_bound;
+  int grid, tiles_rows;
+  int64_t groups;
+  if (mma) {
+    sc.n_tile = pick_mma_n(s, nq);
+    sc.prep.nq_pad = round_up(nq, sc.n_tile);
+    // K is padded to whole 64-byte code boxes (128 dims at 4 bits, 64 at 8)
+    const int box_dims = st.bits1 == 4 ? 128 : 64;
+    sc.prep.kq = (int)ceil_div(st.row1, 64) * box_dims;
+    sc.prep.q16 = c.take<uint16_t>((size_t)sc.prep.nq_pad * sc.prep.kq);
+    grid = s->sm_count;
+    tiles_rows = 128;
+    groups = sc.prep.nq_pad / sc.n_tile;
+  } else {
+    sc.qb = pick_qb(s, nq);
+    grid = fp32_scan_grid(st, sc.qb, s->sm_count);
+    tiles_rows = 256;
+    groups = ceil_div(nq, sc.qb);
+  }
+  const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, tiles_rows);
+  int splits = mma ? s->tuning.mma_splits : s->tuning.fp32_splits;
+  if (splits <= 0) {
+    const int64_t want_items = (int64_t)grid * (mma ? 1 : 2);
+    splits = (int)ceil_div(want_items, groups);
+  }
+  if (splits > ntiles) splits = (int)ntiles;
+  if (splits < 1) splits = 1;
+  sc.plan.splits = splits;
+  sc.plan.n_rows = n_rows;
+  sc.plan.k1 = k1;
+  sc.plan.grid = (int)(groups * splits < grid ? groups * splits : grid);
+  sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
+  const size_t cand = mma ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
+                          : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);
+  sc.plan.cand = c.take<uint64_t>(cand / 8);
+  if (out) *out = sc;
+  return c.off;
+}
+
+// Brackets the launches of one kernel kind with events when profiling is on.
+struct Prof {
+  lvq_store* s;
+  cudaStream_t st;
+  int kind, launches;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Prof(const lvq_store* s_, cudaStream_t st_, int kind_, int launches_ = 1)
+      : s(const_cast<lvq_store*>(s_)), st(st_), kind(kind_), launches(launches_) {
+    if (s->prof_on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, st);
+  }
+  ~Prof() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      s->prof.push_back({kind, launches, a, b});
+    }
+  }
+};
+
+lvq_status check_q(const lvq_store* s, const void* q, int64_t nq) {
+  if (!s) return LVQ_EINVAL;
+  if (nq < 0) return fail(s, LVQ_EINVAL, "nq < 0");
+  if (nq > 0 && !q) return fail(s, LVQ_EINVAL, "null query pointer");
+  if (nq > (int64_t)INT32_MAX) return fail(s, LVQ_EINVAL, "nq too large");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  return LVQ_OK;
+}
+
+lvq_status first_level(lvq_store* s, const float* q, int64_t nq, int k1, int k, bool rerank, int precision,
+                       int64_t* out_ids, float* out_scores, cudaStream_t stream) {
+  const DeviceStore& st = s->ds;
+  bool mma;
+  if (precision == LVQ_FP32) mma = false;
+  else if (precision == LVQ_FP16_MMA || precision == LVQ_AUTO) mma = mma_supported(st);
+  else return fail(s, LVQ_EINVAL, "unknown precision");
+  if (precision == LVQ_FP16_MMA && !mma) return fail(s, LVQ_EINVAL, "tensor-core scan unavailable for this store");
+  std::lock_guard<std::mutex> g(s->mu);
+  const size_t need = plan_scan(s, nq, k1, mma, nullptr, nullptr);
+  lvq_status rc = ensure_ws(s, need);
+  if (rc != LVQ_OK) return rc;
+  ScanScratch sc;
+  plan_scan(s, nq, k1, mma, s->ws, &sc);
+  cudaError_t e;
+  {
+    Prof p(s, stream, LVQ_K_PREP);
+    e = launch_prep_queries(st, q, nq, sc.prep, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "prep_queries");
+  {
+    Prof p(s, stream, mma ? LVQ_K_SCAN_MMA : LVQ_K_SCAN_FP32);
+    if (mma) e = launch_scan_mma(st, nq, sc.prep, sc.n_tile, sc.plan, stream);
+    else e = launch_scan_fp32(st, q, nq, sc.prep, sc.qb, sc.plan, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, mma ? "scan_mma" : "scan_fp32");
+  {
+    Prof p(s, stream, LVQ_K_MERGE);
+    e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, k1, k, rerank, out_ids,
+                            out_scores, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "merge_rerank");
+  return LVQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lvq_status_string(lvq_status st) {
+  switch (st) {
+    case LVQ_OK: return "ok";
+    case LVQ_EINVAL: return "invalid argument";
+    case LVQ_ENOMEM: return "out of device memory";
+    case LVQ_EFULL: return "store full";
+    case LVQ_ENOTFOUND: return "id not live";
+    case LVQ_ECUDA: return "CUDA error";
+    case LVQ_ETIMEOUT: return "device wait timed out";
+    case LVQ_EBUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store** out) {
+  if (!cfg || !means_host || !out) return LVQ_EINVAL;
+  *out = nullptr;
+  if (cfg->d < 1 || cfg->d > kMaxD) return LVQ_EINVAL;
+  if (cfg->bits1 != 4 && cfg->bits1 != 8) return LVQ_EINVAL;
+  if (cfg->bits2 != 0 && cfg->bits2 != 8) return LVQ_EINVAL;
+  if (cfg->n_means < 1 || cfg->n_means > kMaxMeans) return LVQ_EINVAL;
+  if (cfg->metric != LVQ_L2 && cfg->metric != LVQ_IP) return LVQ_EINVAL;
+  if (cfg->reserved != 0) return LVQ_EINVAL;
+  if (cfg->capacity < 1 || cfg->capacity > (int64_t)INT32_MAX) return LVQ_EINVAL;
+  lvq_store* s = new (std::nothrow) lvq_store();
+  if (!s) return LVQ_ENOMEM;
+  s->cfg = *cfg;
+  s->rows_bound = 0;
+  memset(&s->tuning, 0, sizeof(s->tuning));
+  DeviceStore& st = s->ds;
+  memset(&st, 0, sizeof(st));
+  st.d = cfg->d;
+  st.bits1 = cfg->bits1;
+  st.bits2 = cfg->bits2;
+  st.n_means = cfg->n_means;
+  st.metric = cfg->metric;
+  st.capacity = cfg->capacity;
+  st.row1 = (int)round_up(ceil_div((int64_t)cfg->d * cfg->bits1, 8), 32);
+  st.row2 = cfg->bits2 ? (int)round_up(cfg->d, 32) : 0;
+  const int64_t cap = cfg->capacity;
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+  };
+  A((void**)&st.codes1, (size_t)cap * st.row1);
+  if (st.bits2) A((void**)&st.codes2, (size_t)cap * st.row2);
+  A((void**)&st.lower, (size_t)cap * 4);
+  A((void**)&st.step, (size_t)cap * 4);
+  A((void**)&st.norm2, (size_t)cap * 4);
+  A((void**)&st.mean_id, (size_t)round_up(cap, 16));
+  A((void**)&st.live, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
+  A((void**)&st.means, (size_t)cfg->n_means * cfg->d * 4);
+  A((void**)&st.err, 16);
+  A((void**)&s->counters, kCtrWords * 8 + alloc_scratch_bytes(cap));
+  if (e == cudaSuccess) e = cudaMemset(st.live, 0, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
+  if (e == cudaSuccess) e = cudaMemset(st.err, 0, 16);
+  if (e == cudaSuccess) e = cudaMemset(s->counters, 0, kCtrWords * 8);
+  if (e == cudaSuccess) e = cudaMemset(st.codes1, 0, (size_t)cap * st.row1);
+  if (e == cudaSuccess) e = cudaMemcpy(st.means, means_host, (size_t)cfg->n_means * cfg->d * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    lvq_status rc = e == cudaErrorMemoryAllocation ? LVQ_ENOMEM : LVQ_ECUDA;
+    lvq_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return LVQ_OK;
+}
+
+lvq_status lvq_destroy(lvq_store* s) {
+  if (!s) return LVQ_EINVAL;
+  cudaDeviceSynchronize();
+  DeviceStore& st = s->ds;
+  void* ptrs[] = {st.codes1, st.codes2, st.lower, st.step, st.norm2, st.mean_id, st.live, st.means, st.err,
+                  s->counters, s->ws};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+  return LVQ_OK;
+}
+
+lvq_status lvq_encode(const lvq_store* s, const float* x, int64_t n, uint8_t* codes1, uint8_t* codes2,
+                      float* lower, float* step, uint8_t* mean_id, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (n == 0) return LVQ_OK;
+  if (!x || !codes1 || !lower || !step || !mean_id) return fail(s, LVQ_EINVAL, "null pointer");
+  if (s->ds.bits2 && !codes2) return fail(s, LVQ_EINVAL, "codes2 required when bits2 = 8");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  EncodeOut o;
+  o.codes1 = codes1;
+  o.codes2 = s->ds.bits2 ? codes2 : nullptr;
+  o.lower = lower;
+  o.step = step;
+  o.mean_id = mean_id;
+  LVQ_CUDA(s, launch_encode(s->ds, x, n, o, (cudaStream_t)stream), "encode");
+  return LVQ_OK;
+}
+
+lvq_status lvq_insert(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0 || n > s->ds.capacity) return fail(s, LVQ_EINVAL, "n out of range");
+  if (n == 0) return LVQ_OK;
+  if (!x || !out_ids) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t* ctr = s->counters;
+  int32_t* abort_flag = reinterpret_cast<int32_t*>(ctr + kCtrAbort);
+  int32_t* scratch = reinterpret_cast<int32_t*>(ctr + kCtrWords);
+  {
+    Prof p(s, st, LVQ_K_INSERT, 5);
+    LVQ_CUDA(s, launch_alloc_slots(s->ds, n, out_ids, scratch, abort_flag, st), "alloc_slots");
+    EncodeOut o;
+    o.slots = out_ids;
+    o.abort_flag = abort_flag;
+    LVQ_CUDA(s, launch_encode(s->ds, x, n, o, st), "encode(insert)");
+    LVQ_CUDA(s, launch_publish(s->ds, out_ids, n, abort_flag, ctr + kCtrLive, st), "publish");
+  }
+  std::lock_guard<std::mutex> g(s->mu);
+  s->rows_bound = s->rows_bound + n < s->ds.capacity ? s->rows_bound + n : s->ds.capacity;
+  return LVQ_OK;
+}
+
+lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_n_deleted, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (!out_n_deleted || (n > 0 && !ids)) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  int64_t* ctr = s->counters;
+  Prof p(s, (cudaStream_t)stream, LVQ_K_DELETE, n > 0 ? 2 : 1);
+  LVQ_CUDA(s,
+           launch_delete(s->ds, ids, n, out_n_deleted, reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount),
+                         ctr + kCtrLive, (cudaStream_t)stream),
+           "delete");
+  return LVQ_OK;
+}
+
+lvq_status lvq_search_exhaustive(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t k,
+                                 int32_t precision, int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  if (k < 1 || k > kMaxK1) return fail(s, LVQ_EINVAL, "k out of range");
+  if (k1 < 0 || k1 > kMaxK1 || (k1 > 0 && k1 < k)) return fail(s, LVQ_EINVAL, "k1 out of range");
+  if (nq > 0 && (!out_ids || !out_scores)) return fail(s, LVQ_EINVAL, "null output pointer");
+  if (nq == 0) return LVQ_OK;
+  const bool two = s->ds.bits2 && k1 > 0;
+  return first_level(s, q, nq, two ? k1 : k, k, two, precision, out_ids, out_scores, (cudaStream_t)stream);
+}
+
+lvq_status lvq_search_first_level(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t precision,
+                                  int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  if (k1 < 1 || k1 > kMaxK1) return fail(s, LVQ_EINVAL, "k1 out of range");
+  if (nq > 0 && (!out_ids || !out_scores)) return fail(s, LVQ_EINVAL, "null output pointer");
+  if (nq == 0) return LVQ_OK;
+  return first_level(s, q, nq, k1, k1, false, precision, out_ids, out_scores, (cudaStream_t)stream);
+}
+
+lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq, const int64_t* cand,
+                                 int32_t n_cand, int32_t k1, int32_t k, int64_t* out_ids, float* out_scores,
+                                 lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  if (n_cand < 1 || n_cand > kMaxCand) return fail(s, LVQ_EINVAL, "n_cand out of range");
+  if (k < 1 || k > kMaxK1) return fail(s, LVQ_EINVAL, "k out of range");
+  if (k1 < 0 || k1 > kMaxK1 || (k1 > 0 && k1 < k)) return fail(s, LVQ_EINVAL, "k1 out of range");
+  if (nq > 0 && (!cand || !out_ids || !out_scores)) return fail(s, LVQ_EINVAL, "null pointer");
+  if (nq == 0) return LVQ_OK;
+  const DeviceStore& st = s->ds;
+  const bool two = st.bits2 && k1 > 0;
+  std::lock_guard<std::mutex> g(s->mu);
+  Carver c0(nullptr);
+  c0.take<float>(nq);
+  c0.take<float>(nq);
+  c0.take<float>((size_t)nq * st.n_means);
+  rc = ensure_ws(s, c0.off);
+  if (rc != LVQ_OK) return rc;
+  Carver c(s->ws);
+  QueryPrep p;
+  p.qsum = c.take<float>(nq);
+  p.qnorm = c.take<float>(nq);
+  p.cm = c.take<float>((size_t)nq * st.n_means);
+  p.q16 = nullptr;
+  p.nq_pad = nq;
+  p.kq = 0;
+  cudaStream_t str = (cudaStream_t)stream;
+  {
+    Prof pr(s, str, LVQ_K_PREP);
+    LVQ_CUDA(s, launch_prep_queries(st, q, nq, p, str), "prep_queries");
+  }
+  Prof pg(s, str, LVQ_K_GATHER);
+  LVQ_CUDA(s, launch_gather(st, q, nq, p, cand, n_cand, two ? k1 : k, k, two, out_ids, out_scores, str), "gather");
+  return LVQ_OK;
+}
+
+lvq_status lvq_rerank(const lvq_store* cs, const float* q, int64_t nq, const int64_t* ids, int32_t k1, int32_t k,
+                      int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  if (!s->ds.bits2) return fail(s, LVQ_EINVAL, "store has no residual level");
+  if (k1 < 1 || k1 > kMaxRerank || k < 1 || k > k1 || k > kMaxK1) return fail(s, LVQ_EINVAL, "k1/k out of range");
+  if (nq > 0 && (!ids || !out_ids || !out_scores)) return fail(s, LVQ_EINVAL, "null pointer");
+  if (nq == 0) return LVQ_OK;
+  QueryPrep p{};
+  Prof pr(s, (cudaStream_t)stream, LVQ_K_RERANK);
+  LVQ_CUDA(s, launch_rerank(s->ds, q, nq, p, ids, k1, k, out_ids, out_scores, (cudaStream_t)stream), "rerank");
+  return LVQ_OK;
+}
+
+lvq_status lvq_export(const lvq_store* s, const int64_t* ids, int64_t n, uint8_t* codes1, uint8_t* codes2,
+                      float* lower, float* step, uint8_t* mean_id, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (n == 0) return LVQ_OK;
+  if (!ids || !codes1 || !lower || !step || !mean_id) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  LVQ_CUDA(s, launch_export(s->ds, ids, n, codes1, codes2, lower, step, mean_id, (cudaStream_t)stream), "export");
+  return LVQ_OK;
+}
+
+lvq_status lvq_stats(const lvq_store* s, int64_t* n_live_host, lvq_stream_t stream) {
+  if (!s || !n_live_host) return LVQ_EINVAL;
+  LVQ_CUDA(s, cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  int64_t live = 0;
+  int32_t err = 0;
+  LVQ_CUDA(s, cudaMemcpy(&live, s->counters + kCtrLive, 8, cudaMemcpyDeviceToHost), "read counters");
+  LVQ_CUDA(s, cudaMemcpy(&err, s->ds.err, 4, cudaMemcpyDeviceToHost), "read error word");
+  *n_live_host = live;
+  if (err) {
+    LVQ_CUDA(s, cudaMemset(s->ds.err, 0, 4), "clear error word");
+    return fail(s, (lvq_status)err, lvq_status_string((lvq_status)err));
+  }
+  return LVQ_OK;
+}
+
+lvq_status lvq_reserve(lvq_store* s, int64_t max_nq, int32_t max_k1, int32_t max_cand) {
+  if (!s || max_nq < 0 || max_k1 < 1 || max_k1 > kMaxK1 || max_cand < 0) return LVQ_EINVAL;
+  (void)max_cand;
+  std::lock_guard<std::mutex> g(s->mu);
+  size_t need = plan_scan(s, max_nq, max_k1, false, nullptr, nullptr);
+  if (mma_supported(s->ds)) {
+    const size_t m = plan_scan(s, max_nq, max_k1, true, nullptr, nullptr);
+    if (m > need) need = m;
+  }
+  return ensure_ws(s, need);
+}
+
+lvq_status lvq_set_tuning(lvq_store* s, const lvq_tuning* t) {
+  if (!s || !t) return LVQ_EINVAL;
+  if (t->mma_n != 0 && t->mma_n != 16 && t->mma_n != 32 && t->mma_n != 64 && t->mma_n != 128) return LVQ_EINVAL;
+  if (t->fp32_q != 0 && t->fp32_q != 1 && t->fp32_q != 2 && t->fp32_q != 4 && t->fp32_q != 8 && t->fp32_q != 16)
+    return LVQ_EINVAL;
+  if (t->mma_splits < 0 || t->fp32_splits < 0) return LVQ_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  s->tuning = *t;
+  return LVQ_OK;
+}
+
+lvq_status lvq_get_tuning(const lvq_store* s, lvq_tuning* t) {
+  if (!s || !t) return LVQ_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  *t = s->tuning;
+  return LVQ_OK;
+}
+
+lvq_status lvq_profile_enable(lvq_store* s, int32_t on) {
+  if (!s) return LVQ_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  s->prof_on = on != 0;
+  return LVQ_OK;
+}
+
+lvq_status lvq_profile_read(lvq_store* s, double* ms, int64_t* launches, int32_t n_kinds) {
+  if (!s || !ms || !launches || n_kinds < 1 || n_kinds > LVQ_KERNEL_KINDS) return LVQ_EINVAL;
+  std::lock_guard<std::mutex> g(s->mu);
+  LVQ_CUDA(s, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  for (int i = 0; i < n_kinds; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  for (auto& r : s->prof) {
+    float t = 0.0f;
+    if (r.kind < n_kinds && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ms[r.kind] += t;
+      launches[r.kind] += r.launches;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  s->prof.clear();
+  return LVQ_OK;
+}
+
+lvq_status lvq_last_error(const lvq_store* s, char* buf, size_t len) {
+  if (!s) return LVQ_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  lvq_status rc = LVQ_OK;
+  std::string msg;
+  if (e != cudaSuccess) {
+    rc = LVQ_ECUDA;
+    msg = cudaGetErrorString(e);
+  } else {
+    int32_t err = 0;
+    if (cudaMemcpy(&err, s->ds.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+      rc = (lvq_status)err;
+      msg = lvq_status_string(rc);
+      cudaMemset(s->ds.err, 0, 4);
+    } else {
+      std::lock_guard<std::mutex> g(s->mu);
+      msg = s->last_msg;
+    }
+  }
+  if (buf && len) {
+    strncpy(buf, msg.c_str(), len - 1);
+    buf[len - 1] = 0;
+  }
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Float32 LVQ scoring helpers (Sec. 3.2) shared by the CUDA-core kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "topk.cuh"
+
+namespace lvq {
+
+// Code offset used to centre first-level codes before multiplying them with
+// a query: c - 2^(B1-1) lies in [-2^(B1-1), 2^(B1-1) - 1], which halves the
+// magnitude of the partial sums.  The offset is folded back into the
+// per-vector constant:  <q, l + D c> = (l + off*D) sum(q) + D <q, c - off>.
+__host__ __device__ inline float code_offset(int bits1) { return bits1 == 4 ? 8.0f : 128.0f; }
+
+// exact float of (code - off) for the 16-bit integers in the low / high half
+__device__ __forceinline__ float lo_centred(uint32_t t, float magic_plus_off) {
+  return __uint_as_float(__byte_perm(t, 0x4B000000u, 0x7610)) - magic_plus_off;
+}
+__device__ __forceinline__ float hi_centred(uint32_t t, float magic_plus_off) {
+  return __uint_as_float(__byte_perm(t, 0x4B000000u, 0x7632)) - magic_plus_off;
+}
+__device__ __forceinline__ float byte_centred(uint32_t w, int i, float magic_plus_off) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440 + i)) - magic_plus_off;
+}
+
+// Decode the 8 first-level codes of group g (dims 8g..8g+7) of a stored row
+// into floats minus `sub` (sub = 2^23 for the raw code, 2^23 + off centred).
+__device__ __forceinline__ void group_codes(const uint8_t* row, int bits1, int g, float sub, float (&c)[8]) {
+  if (bits1 == 4) {
+    const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(row) + g);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const uint32_t t = nib_pair(w, p);
+      c[2 * p] = lo_centred(t, sub);
+      c[2 * p + 1] = hi_centred(t, sub);
+    }
+  } else {
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(row) + g);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[i] = byte_centred(w.x, i, sub);
+      c[4 + i] = byte_centred(w.y, i, sub);
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Two-level float32 score of slot s, computed by one warp (result valid in
+// every lane).  x2_j = mu_mj + (l + D c_j) + (l2 + D2 c2_j), l2 = -D/2,
+// D2 = D/255; L2: sum (q_j - x2_j)^2, IP: sum q_j x2_j.  q is in shared memory.
+__device__ __forceinline__ float score2_warp(const DeviceStore& st, int64_t s, const float* qsh) {
+  const int lane = threadIdx.x & 31;
+  const int d = st.d;
+  const int groups = (d + 7) >> 3;
+  const float lo = __ldg(st.lower + s), step = __ldg(st.step + s);
+  const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+  const float* mu = st.means + (int64_t)__ldg(st.mean_id + s) * d;
+  const uint8_t* row1 = st.codes1 + s * st.row1;
+  const uint8_t* row2 = st.codes2 + s * st.row2;
+  float acc = 0.0f;
+  for (int g = lane; g < groups; g += 32) {
+    float c[8];
+    group_codes(row1, st.bits1, g, 8388608.0f, c);
+    const uint2 w2 = __ldg(reinterpret_cast<const uint2*>(row2) + g);
+    float part = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = g * 8 + e;
+      if (j < d) {
+        const float c2 = byte_centred(e < 4 ? w2.x : w2.y, e & 3, 8388608.0f);
+        const float x2 = __fadd_rn(__fadd_rn(__fmaf_rn(step, c[e], lo), __fmaf_rn(step2, c2, lo2)), __ldg(mu + j));
+        if (st.metric == LVQ_L2) {
+          const float df = qsh[j] - x2;
+          part = __fmaf_rn(df, df, part);
+        } else {
+          part = __fmaf_rn(qsh[j], x2, part);
+        }
+      }
+    }
+    acc += part;
+  }
+  return warp_sum(acc);
+}
+
+}  // namespace lvq

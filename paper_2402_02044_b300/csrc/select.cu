@@ -1,0 +1,326 @@
+// Query preparation, merging of per-split top-k1 lists, residual re-ranking
+// (Sec. 2.2, App. C) and the ID-gather search (the frontier-scoring step of
+// greedy graph search, Alg. 1).
+#include "kernels.cuh"
+#include "score.cuh"
+
+namespace lvq {
+
+namespace {
+
+// ---- query preparation (one warp per query) ---------------------------------
+__global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
+                                                   QueryPrep p) {
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int d = st.d;
+  const int64_t rows = p.q16 ? (p.nq_pad > nq ? p.nq_pad : nq) : nq;
+  for (int64_t i = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); i < rows; i += (int64_t)gridDim.x * warps) {
+    const bool real = i < nq;
+    if (p.q16) {
+      __half* dst = reinterpret_cast<__half*>(p.q16) + i * p.kq;
+      for (int j = lane; j < p.kq; j += 32)
+        dst[j] = (real && j < d) ? __float2half_rn(q[i * d + j]) : __float2half_rn(0.0f);
+    }
+    if (!real) continue;
+    const float* qi = q + i * d;
+    float s = 0.0f, s2 = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+      const float v = qi[j];
+      s += v;
+      s2 = __fmaf_rn(v, v, s2);
+    }
+    s = warp_sum(s);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      p.qsum[i] = s;
+      p.qnorm[i] = s2;
+    }
+    for (int m = 0; m < st.n_means; ++m) {
+      const float* mu = st.means + (int64_t)m * d;
+      float c = 0.0f;
+      for (int j = lane; j < d; j += 32) c = __fmaf_rn(qi[j], __ldg(mu + j), c);
+      c = warp_sum(c);
+      if (lane == 0) p.cm[i * st.n_means + m] = c;
+    }
+  }
+}
+
+// ---- shared re-rank tail -------------------------------------------------------
+// keys[0..n) hold candidate keys (sorted or not, possibly with repeats).  Each
+// warp scores candidates with both levels; the block then sorts the new keys
+// and writes the k best.  scratch: pow2_at_least(n) keys of shared memory.
+__device__ void rerank_tail(const DeviceStore& st, const float* qsh, const uint64_t* keys, int n, int k,
+                            uint64_t* scratch, int* sh_pos, int64_t* out_ids, float* out_scores) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int np2 = pow2_at_least(n < 1 ? 1 : n);
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) scratch[i] = kNoKey;
+  __syncthreads();
+  for (int i = wid; i < n; i += nw) {
+    const uint64_t key = keys[i];
+    if (key == kNoKey) continue;
+    const uint32_t s = (uint32_t)key;
+    const float sc = score2_warp(st, s, qsh);
+    if (lane == 0) scratch[i] = make_key(sc, s, st.metric);
+  }
+  __syncthreads();
+  block_sort(scratch, np2);
+  write_results(scratch, np2, k, st.metric, out_ids, out_scores, sh_pos);
+}
+
+// ---- merge of per-split lists + optional re-rank (one block per query) --------
+constexpr int kMergeThreads = 128;
+
+__global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore st, const float* __restrict__ q,
+                                                                      const uint64_t* __restrict__ partial,
+                                                                      int splits, int k1, int k, int rerank,
+                                                                      int64_t* out_ids, float* out_scores) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int qi = blockIdx.x;
+  const int cap = pow2_at_least(k1 + kMergeThreads);
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* scratch = buf + cap;                   // pow2_at_least(k1) keys
+  float* qsh = reinterpret_cast<float*>(scratch + pow2_at_least(k1));
+  int* sh_pos = reinterpret_cast<int*>(qsh + st.d);
+  __shared__ int cnt;
+  __shared__ uint64_t thr;
+  __shared__ int hist[256];
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    thr = kNoKey;
+  }
+  for (int j = threadIdx.x; j < st.d; j += blockDim.x) qsh[j] = q[(int64_t)qi * st.d + j];
+  __syncthreads();
+  const uint64_t* src = partial + (int64_t)qi * splits * k1;
+  const int total = splits * k1;
+  for (int base = 0; base < total; base += kMergeThreads) {
+    const int i = base + threadIdx.x;
+    if (i < total) {
+      const uint64_t key = src[i];
+      if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+    }
+    __syncthreads();
+    if (cnt > cap - kMergeThreads) {
+      if (threadIdx.x < 32) {
+        uint64_t t;
+        const int kept = warp_select(buf, cnt, k1, hist, &t);
+        if (threadIdx.x == 0) {
+          cnt = kept;
+          thr = t;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < 32) {
+    uint64_t t;
+    const int kept = warp_select(buf, cnt, k1, hist, &t);
+    if (threadIdx.x == 0) cnt = kept;
+  }
+  __syncthreads();
+  const int n1 = cnt;
+  const int np2 = pow2_at_least(k1);
+  for (int i = n1 + threadIdx.x; i < np2; i += blockDim.x) buf[i] = kNoKey;
+  block_sort(buf, np2);
+  int64_t* oi = out_ids + (int64_t)qi * k;
+  float* os = out_scores + (int64_t)qi * k;
+  if (!rerank) {
+    write_results(buf, n1, k, st.metric, oi, os, sh_pos);
+    return;
+  }
+  rerank_tail(st, qsh, buf, n1, k, scratch, sh_pos, oi, os);
+}
+
+// ---- re-rank of caller-given candidates (one block per query) -----------------
+__global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float* __restrict__ q,
+                                                      const int64_t* __restrict__ ids, int k1, int k,
+                                                      int64_t* out_ids, float* out_scores) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int qi = blockIdx.x;
+  const int np2 = pow2_at_least(k1);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* scratch = keys + np2;
+  float* qsh = reinterpret_cast<float*>(scratch + np2);
+  int* sh_pos = reinterpret_cast<int*>(qsh + st.d);
+  for (int j = threadIdx.x; j < st.d; j += blockDim.x) qsh[j] = q[(int64_t)qi * st.d + j];
+  for (int i = threadIdx.x; i < k1; i += blockDim.x) {
+    const int64_t s = ids[(int64_t)qi * k1 + i];
+    const bool ok = s >= 0 && s < st.capacity && is_live(st.live, s);
+    keys[i] = ok ? (uint64_t)s : kNoKey;  // the score is filled in by rerank_tail
+  }
+  __syncthreads();
+  rerank_tail(st, qsh, keys, k1, k, scratch, sh_pos, out_ids + (int64_t)qi * k, out_scores + (int64_t)qi * k);
+}
+
+// ---- ID-gather search (one block per query, one thread per candidate) ---------
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, const float* __restrict__ q,
+                                                                 QueryPrep p, const int64_t* __restrict__ cand,
+                                                                 int n_cand, int k1, int k, int rerank,
+                                                                 int64_t* out_ids, float* out_scores) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int qi = blockIdx.x;
+  const int d = st.d;
+  const int stage1 = rerank ? k1 : k;
+  const int cap = pow2_at_least(stage1 + kGatherThreads);
+  const int groups = (d + 7) >> 3;
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* scratch = buf + cap;
+  float* qsh = reinterpret_cast<float*>(scratch + pow2_at_least(stage1));
+  uint64_t* tmp = reinterpret_cast<uint64_t*>(qsh + groups * 8 * 2);  // cap keys
+  float* qc = qsh + groups * 8;  // centred / shifted copy used by the first level
+  int* sh_pos = reinterpret_cast<int*>(tmp + cap);
+  __shared__ int cnt;
+  __shared__ uint64_t thr;
+  __shared__ int scan_sh[kGatherThreads / 32 + 1];
+  const bool ip = st.metric == LVQ_IP;
+  const bool one_mean = st.n_means == 1;
+  for (int j = threadIdx.x; j < groups * 8; j += blockDim.x) {
+    const float v = j < d ? q[(int64_t)qi * d + j] : 0.0f;
+    qsh[j] = v;
+    qc[j] = (!ip && one_mean && j < d) ? __fsub_rn(v, st.means[j]) : v;
+  }
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    thr = kNoKey;
+  }
+  __syncthreads();
+  const float off = code_offset(st.bits1);
+  const float qs = ip ? p.qsum[qi] : 0.0f;
+  const float* cmq = ip ? p.cm + (int64_t)qi * st.n_means : nullptr;
+  const int64_t* cl = cand + (int64_t)qi * n_cand;
+  for (int base = 0; base < n_cand; base += kGatherThreads) {
+    const int i = base + threadIdx.x;
+    if (i < n_cand) {
+      const int64_t s = cl[i];
+      if (s >= 0 && s < st.capacity && is_live(st.live, s)) {
+        const uint8_t* row = st.codes1 + s * st.row1;
+        const float lo = __ldg(st.lower + s), step = __ldg(st.step + s);
+        const int m = __ldg(st.mean_id + s);
+        float sc;
+        if (ip) {
+          float acc = 0.0f;
+          for (int g = 0; g < groups; ++g) {
+            float c[8];
+            group_codes(row, st.bits1, g, 8388608.0f + off, c);
+            float part = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) part = __fmaf_rn(qc[g * 8 + e], c[e], part);
+            acc += part;
+          }
+          sc = __fmaf_rn(step, acc, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[m]));
+        } else {
+          const float* mu = st.means + (int64_t)m * d;
+          float acc = 0.0f;
+          for (int g = 0; g < groups; ++g) {
+            float c[8];
+            group_codes(row, st.bits1, g, 8388608.0f, c);
+            float part = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int j = g * 8 + e;
+              if (j < d) {
+                float xh = __fmaf_rn(step, c[e], lo);
+                if (!one_mean) xh = __fadd_rn(xh, __ldg(mu + j));
+                const float df = qc[j] - xh;
+                part = __fmaf_rn(df, df, part);
+              }
+            }
+            acc += part;
+          }
+          sc = acc;
+        }
+        const uint64_t key = make_key(sc, (uint32_t)s, st.metric);
+        if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+      }
+    }
+    __syncthreads();
+    if (cnt > cap - kGatherThreads) {
+      uint64_t t;
+      const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
+      if (threadIdx.x == 0) {
+        cnt = kept;
+        thr = t;
+      }
+      __syncthreads();
+    }
+  }
+  {
+    uint64_t t;
+    const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
+    if (threadIdx.x == 0) cnt = kept;
+    __syncthreads();
+  }
+  int64_t* oi = out_ids + (int64_t)qi * k;
+  float* os = out_scores + (int64_t)qi * k;
+  if (!rerank) {
+    write_results(buf, cnt, k, st.metric, oi, os, sh_pos);
+    return;
+  }
+  rerank_tail(st, qsh, buf, cnt, k, scratch, sh_pos, oi, os);
+}
+
+}  // namespace
+
+cudaError_t launch_prep_queries(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                                cudaStream_t stream) {
+  const int64_t rows = p.q16 ? (p.nq_pad > nq ? p.nq_pad : nq) : nq;
+  if (rows <= 0) return cudaSuccess;
+  const int blocks = (int)(ceil_div(rows, 8) < 65536 ? ceil_div(rows, 8) : 65536);
+  prep_kernel<<<blocks, 256, 0, stream>>>(st, q, nq, p);
+  return cudaGetLastError();
+}
+
+static size_t merge_smem(int d, int k1) {
+  return (size_t)(pow2_at_least(k1 + kMergeThreads) + pow2_at_least(k1)) * 8 + (size_t)d * 4 +
+         (size_t)(k1 + 2) * 4 + 16;
+}
+
+cudaError_t launch_merge_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep&,
+                                const uint64_t* partial, int splits, int k1, int k, bool rerank,
+                                int64_t* out_ids, float* out_scores, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const size_t sm = merge_smem(st.d, k1 > k ? k1 : k);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(merge_rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  merge_rerank_kernel<<<(unsigned)nq, kMergeThreads, sm, stream>>>(st, q, partial, splits, k1, k, rerank ? 1 : 0,
+                                                                   out_ids, out_scores);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep&, const int64_t* ids,
+                          int k1, int k, int64_t* out_ids, float* out_scores, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const size_t sm = (size_t)pow2_at_least(k1) * 16 + (size_t)st.d * 4 + (size_t)(k + 2) * 4 + 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  rerank_kernel<<<(unsigned)nq, 256, sm, stream>>>(st, q, ids, k1, k, out_ids, out_scores);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                          const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
+                          float* out_scores, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const int stage1 = rerank ? k1 : k;
+  const int groups = (st.d + 7) / 8;
+  const size_t sm = (size_t)(2 * pow2_at_least(stage1 + kGatherThreads) + pow2_at_least(stage1)) * 8 +
+                    (size_t)groups * 8 * 4 * 2 + (size_t)(k + 2) * 4 + 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  gather_kernel<<<(unsigned)nq, kGatherThreads, sm, stream>>>(st, q, p, cand, n_cand, k1, k, rerank ? 1 : 0,
+                                                              out_ids, out_scores);
+  return cudaGetLastError();
+}
+
+}  // namespace lvq

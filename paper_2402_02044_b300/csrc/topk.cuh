@@ -1,0 +1,222 @@
+// Top-k selection on 64-bit (score, id) keys.
+//
+// The scans and merges keep, per query, a "candidate buffer": keys better
+// than a running threshold are appended; when the buffer may overflow, one
+// warp finds the k-th smallest key by a most-significant-digit radix select
+// (8-bit digits, a 256-bin histogram in shared memory), keeps the keys not
+// above it and makes it the new threshold.  Final lists are sorted by a
+// bitonic sort in shared memory.
+#pragma once
+
+#include "lvq_internal.cuh"
+
+namespace lvq {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ inline int pow2_at_least(int v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// k-th smallest (1-based, 1 <= k <= n) of the n distinct keys buf[0..n),
+// found by one whole warp.  hist: 256 ints of shared memory owned by the warp.
+__device__ __forceinline__ uint64_t warp_kth(const uint64_t* buf, int n, int k, int* hist) {
+  const int lane = threadIdx.x & 31;
+  uint64_t prefix = 0, mask = 0;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint64_t key = buf[i];
+      if ((key & mask) == prefix) atomicAdd(&hist[(int)((key >> shift) & 255u)], 1);
+    }
+    __syncwarp();
+    int c[8], s = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      c[e] = hist[lane * 8 + e];
+      s += c[e];
+    }
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - s;
+    const bool mine = excl < k && k <= incl;
+    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+    int bin = 0, before = 0, inbin = 0;
+    if (mine) {
+      int run = excl;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        if (run < k && k <= run + c[e] && inbin == 0) {
+          bin = lane * 8 + e;
+          before = run;
+          inbin = c[e];
+        }
+        run += c[e];
+      }
+    }
+    bin = __shfl_sync(kFull, bin, src);
+    before = __shfl_sync(kFull, before, src);
+    inbin = __shfl_sync(kFull, inbin, src);
+    k -= before;
+    prefix |= (uint64_t)bin << shift;
+    mask |= 255ull << shift;
+    __syncwarp();
+    if (inbin == 1) {
+      // a single key carries this prefix: it is the answer
+      uint64_t found = 0;
+      for (int i = lane; i < n; i += 32) {
+        const uint64_t key = buf[i];
+        if ((key & mask) == prefix) found = key;
+      }
+      // the matching key is the only candidate that is not 0 (a key of 0
+      // would equal the prefix, which is then returned all the same)
+      uint64_t r = found;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(kFull, r, o);
+        r = r > y ? r : y;
+      }
+      return (r & mask) == prefix ? r : prefix;
+    }
+  }
+  return prefix;
+}
+
+// Keep the k smallest of the n distinct keys buf[0..n) at buf[0..kept),
+// unsorted; returns kept = min(n, k) and sets *thr to the k-th smallest key
+// when n >= k (else kNoKey).  One whole warp.
+__device__ __forceinline__ int warp_select(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  const int lane = threadIdx.x & 31;
+  if (n <= k) {
+    *thr = (n == k && k > 0) ? warp_kth(buf, n, k, hist) : kNoKey;
+    __syncwarp();
+    return n;
+  }
+  const uint64_t t = warp_kth(buf, n, k, hist);
+  int pos = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint64_t key = i < n ? buf[i] : kNoKey;
+    const bool keep = i < n && key <= t;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    __syncwarp();
+    if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = key;
+    pos += __popc(bal);
+    __syncwarp();
+  }
+  *thr = t;
+  return pos;
+}
+
+// Ascending bitonic sort of keys[0..n) in shared memory, n a power of two;
+// called by all threads of the block.
+__device__ __forceinline__ void block_sort(uint64_t* keys, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1));  // lower index of the pair
+        const int p = i + j;
+        const bool up = (i & k) == 0;
+        const uint64_t a = keys[i], b = keys[p];
+        if ((a > b) == up) {
+          keys[i] = b;
+          keys[p] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+  // sh: blockDim/32 ints of shared memory
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) sh[lane] = s;
+  }
+  __syncthreads();
+  const int before = (wid ? sh[wid - 1] : 0) + x - v;
+  total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+// Block-wide: sort buf[0..cap) (entries from n on are overwritten with
+// kNoKey), drop repeated keys, keep the k best at buf[0..kept) in ascending
+// order.  tmp: cap keys of shared memory; sh: blockDim/32 + 1 ints.
+// Returns kept; *thr = k-th best key if k were kept, else kNoKey.
+__device__ __forceinline__ int block_select_dedupe(uint64_t* buf, uint64_t* tmp, int cap, int n, int k, int* sh,
+                                                   uint64_t* thr) {
+  for (int i = n + threadIdx.x; i < cap; i += blockDim.x) buf[i] = kNoKey;
+  block_sort(buf, cap);
+  int written = 0;
+  for (int base = 0; base < cap; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint64_t key = i < cap ? buf[i] : kNoKey;
+    const bool keep = i < cap && key != kNoKey && (i == 0 || key != buf[i - 1]);
+    int total;
+    const int pos = written + block_exclusive_scan(keep ? 1 : 0, sh, total);
+    if (keep) tmp[pos] = key;
+    written += total;
+  }
+  __syncthreads();
+  const int kept = written < k ? written : k;
+  for (int i = threadIdx.x; i < kept; i += blockDim.x) buf[i] = tmp[i];
+  __syncthreads();
+  *thr = (kept == k && k > 0) ? buf[k - 1] : kNoKey;
+  return kept;
+}
+
+// Write the k best of the sorted keys[0..n) (repeats skipped) as (id, score),
+// padding with (-1, +/-inf).  Called by all threads of the block; sh_pos:
+// k + 1 ints of shared memory.
+__device__ __forceinline__ void write_results(const uint64_t* keys, int n, int k, int metric, int64_t* out_ids,
+                                              float* out_scores, int* sh_pos) {
+  if (threadIdx.x == 0) {
+    int w = 0;
+    for (int i = 0; i < n && w < k; ++i) {
+      if (keys[i] == kNoKey) break;
+      if (i && keys[i] == keys[i - 1]) continue;
+      sh_pos[w++] = i;
+    }
+    sh_pos[k] = w;
+  }
+  __syncthreads();
+  const int w = sh_pos[k];
+  const float pad = metric == LVQ_IP ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    if (i < w) {
+      const uint64_t key = keys[sh_pos[i]];
+      out_ids[i] = (int64_t)(uint32_t)key;
+      out_scores[i] = key_score(key, metric);
+    } else {
+      out_ids[i] = -1;
+      out_scores[i] = pad;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace lvq

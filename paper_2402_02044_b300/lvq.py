@@ -1,0 +1,324 @@
+"""Python binding of the LVQ C ABI (include/lvq.h), via ctypes.
+
+Argument marshalling only: every function below checks the tensors it is
+given (device, dtype, contiguity), passes raw device pointers and the current
+CUDA stream to the function of the same name in liblvq.so, and turns a
+non-zero status into an ``LVQError``.  All computation happens in the
+library's CUDA kernels; there is no fallback.  PyTorch provides device memory
+and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblvq.so")
+
+LVQ_OK, LVQ_EINVAL, LVQ_ENOMEM, LVQ_EFULL, LVQ_ENOTFOUND, LVQ_ECUDA, LVQ_ETIMEOUT, LVQ_EBUSY = range(8)
+LVQ_L2, LVQ_IP = 0, 1
+LVQ_FP32, LVQ_FP16_MMA, LVQ_AUTO = 0, 1, 2
+
+METRICS = {"l2": LVQ_L2, "ip": LVQ_IP}
+PRECISIONS = {"fp32": LVQ_FP32, "fp16": LVQ_FP16_MMA, "auto": LVQ_AUTO}
+
+
+class lvq_config(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
+                ("n_means", ctypes.c_int32), ("metric", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("capacity", ctypes.c_int64)]
+
+
+class lvq_tuning(ctypes.Structure):
+    _fields_ = [("mma_n", ctypes.c_int32), ("mma_splits", ctypes.c_int32), ("fp32_q", ctypes.c_int32),
+                ("fp32_splits", ctypes.c_int32)]
+
+
+class LVQError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SIGS = {
+    "lvq_create": [ctypes.POINTER(lvq_config), _P, ctypes.POINTER(_P)],
+    "lvq_destroy": [_P],
+    "lvq_encode": [_P, _P, _I64, _P, _P, _P, _P, _P, _P],
+    "lvq_insert": [_P, _P, _I64, _P, _P],
+    "lvq_delete": [_P, _P, _I64, _P, _P],
+    "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
+    "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
+    "lvq_search_candidates": [_P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P],
+    "lvq_rerank": [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P],
+    "lvq_export": [_P, _P, _I64, _P, _P, _P, _P, _P, _P],
+    "lvq_stats": [_P, ctypes.POINTER(_I64), _P],
+    "lvq_reserve": [_P, _I64, _I32, _I32],
+    "lvq_set_tuning": [_P, ctypes.POINTER(lvq_tuning)],
+    "lvq_get_tuning": [_P, ctypes.POINTER(lvq_tuning)],
+    "lvq_last_error": [_P, ctypes.c_char_p, ctypes.c_size_t],
+    "lvq_profile_enable": [_P, _I32],
+    "lvq_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
+}
+
+KERNEL_KINDS = ["prep", "scan_fp32", "scan_mma", "merge", "gather", "rerank", "insert", "delete"]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblvq.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing; build it with paper_2402_02044_b300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lvq_status_string.argtypes = [ctypes.c_int]
+    lib.lvq_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().lvq_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != LVQ_OK:
+        raise LVQError(status, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype, name: str, allow_none: bool = False) -> Optional[int]:
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+# --------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# --------------------------------------------------------------------------
+
+def lvq_create(d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int) -> int:
+    means = np.ascontiguousarray(means, dtype=np.float32).reshape(-1, d)
+    cfg = lvq_config(d, bits1, bits2, len(means), METRICS[metric], 0, capacity)
+    out = _P()
+    _check(load().lvq_create(ctypes.byref(cfg), means.ctypes.data_as(_P), ctypes.byref(out)), "lvq_create")
+    return out.value
+
+
+def lvq_destroy(store: int):
+    _check(load().lvq_destroy(store), "lvq_destroy")
+
+
+def lvq_encode(store, x, codes1, codes2, lower, step, mean_id, stream=None):
+    n = x.shape[0]
+    _check(load().lvq_encode(store, _ptr(x, torch.float32, "x"), n, _ptr(codes1, torch.uint8, "codes1"),
+                             _ptr(codes2, torch.uint8, "codes2", True), _ptr(lower, torch.float32, "lower"),
+                             _ptr(step, torch.float32, "step"), _ptr(mean_id, torch.uint8, "mean_id"),
+                             _stream(stream)), "lvq_encode")
+
+
+def lvq_insert(store, x, out_ids, stream=None):
+    _check(load().lvq_insert(store, _ptr(x, torch.float32, "x"), x.shape[0], _ptr(out_ids, torch.int64, "out_ids"),
+                             _stream(stream)), "lvq_insert")
+
+
+def lvq_delete(store, ids, out_n_deleted, stream=None):
+    _check(load().lvq_delete(store, _ptr(ids, torch.int64, "ids"), ids.numel(),
+                             _ptr(out_n_deleted, torch.int64, "out_n_deleted"), _stream(stream)), "lvq_delete")
+
+
+def lvq_search_exhaustive(store, q, k1, k, precision, out_ids, out_scores, stream=None):
+    _check(load().lvq_search_exhaustive(store, _ptr(q, torch.float32, "q"), q.shape[0], k1, k,
+                                        PRECISIONS.get(precision, precision), _ptr(out_ids, torch.int64, "out_ids"),
+                                        _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
+           "lvq_search_exhaustive")
+
+
+def lvq_search_first_level(store, q, k1, precision, out_ids, out_scores, stream=None):
+    _check(load().lvq_search_first_level(store, _ptr(q, torch.float32, "q"), q.shape[0], k1,
+                                         PRECISIONS.get(precision, precision), _ptr(out_ids, torch.int64, "out_ids"),
+                                         _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
+           "lvq_search_first_level")
+
+
+def lvq_search_candidates(store, q, cand, k1, k, out_ids, out_scores, stream=None):
+    _check(load().lvq_search_candidates(store, _ptr(q, torch.float32, "q"), q.shape[0],
+                                        _ptr(cand, torch.int64, "cand"), cand.shape[1], k1, k,
+                                        _ptr(out_ids, torch.int64, "out_ids"),
+                                        _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
+           "lvq_search_candidates")
+
+
+def lvq_rerank(store, q, ids, k, out_ids, out_scores, stream=None):
+    _check(load().lvq_rerank(store, _ptr(q, torch.float32, "q"), q.shape[0], _ptr(ids, torch.int64, "ids"),
+                             ids.shape[1], k, _ptr(out_ids, torch.int64, "out_ids"),
+                             _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)), "lvq_rerank")
+
+
+def lvq_export(store, ids, codes1, codes2, lower, step, mean_id, stream=None):
+    _check(load().lvq_export(store, _ptr(ids, torch.int64, "ids"), ids.numel(), _ptr(codes1, torch.uint8, "codes1"),
+                             _ptr(codes2, torch.uint8, "codes2", True), _ptr(lower, torch.float32, "lower"),
+                             _ptr(step, torch.float32, "step"), _ptr(mean_id, torch.uint8, "mean_id"),
+                             _stream(stream)), "lvq_export")
+
+
+def lvq_stats(store, stream=None) -> int:
+    live = _I64()
+    _check(load().lvq_stats(store, ctypes.byref(live), _stream(stream)), "lvq_stats")
+    return live.value
+
+
+def lvq_reserve(store, max_nq: int, max_k1: int, max_cand: int = 0):
+    _check(load().lvq_reserve(store, max_nq, max_k1, max_cand), "lvq_reserve")
+
+
+def lvq_set_tuning(store, mma_n=0, mma_splits=0, fp32_q=0, fp32_splits=0):
+    t = lvq_tuning(mma_n, mma_splits, fp32_q, fp32_splits)
+    _check(load().lvq_set_tuning(store, ctypes.byref(t)), "lvq_set_tuning")
+
+
+def lvq_get_tuning(store) -> dict:
+    t = lvq_tuning()
+    _check(load().lvq_get_tuning(store, ctypes.byref(t)), "lvq_get_tuning")
+    return dict(mma_n=t.mma_n, mma_splits=t.mma_splits, fp32_q=t.fp32_q, fp32_splits=t.fp32_splits)
+
+
+def lvq_profile_enable(store, on: bool = True):
+    _check(load().lvq_profile_enable(store, 1 if on else 0), "lvq_profile_enable")
+
+
+def lvq_profile_read(store) -> dict:
+    n = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (_I64 * n)()
+    _check(load().lvq_profile_read(store, ms, cnt, n), "lvq_profile_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def lvq_last_error(store) -> tuple[int, str]:
+    buf = ctypes.create_string_buffer(512)
+    st = load().lvq_last_error(store, buf, 512)
+    return st, buf.value.decode()
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper: owns the handle and allocates output tensors
+# --------------------------------------------------------------------------
+
+class Store:
+    """A device-resident LVQ store (thin wrapper over the C ABI)."""
+
+    def __init__(self, d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int):
+        self.d, self.bits1, self.bits2, self.metric, self.capacity = d, bits1, bits2, metric, capacity
+        self.means = np.ascontiguousarray(means, dtype=np.float32).reshape(-1, d)
+        self.handle = lvq_create(d, bits1, bits2, self.means, metric, capacity)
+
+    def close(self):
+        if self.handle:
+            lvq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return torch.device("cuda", torch.cuda.current_device())
+
+    def encode(self, x: torch.Tensor, stream=None):
+        n = x.shape[0]
+        dev = x.device
+        c1 = torch.empty((n, self.d), dtype=torch.uint8, device=dev)
+        c2 = torch.empty((n, self.d), dtype=torch.uint8, device=dev) if self.bits2 else None
+        lo = torch.empty(n, dtype=torch.float32, device=dev)
+        st = torch.empty(n, dtype=torch.float32, device=dev)
+        mid = torch.empty(n, dtype=torch.uint8, device=dev)
+        lvq_encode(self.handle, x, c1, c2, lo, st, mid, stream)
+        return dict(codes1=c1, codes2=c2, lower=lo, step=st, mean_id=mid)
+
+    def insert(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        ids = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
+        lvq_insert(self.handle, x, ids, stream)
+        return ids
+
+    def delete(self, ids: torch.Tensor, stream=None) -> torch.Tensor:
+        out = torch.empty(1, dtype=torch.int64, device=ids.device)
+        lvq_delete(self.handle, ids, out, stream)
+        return out
+
+    def search(self, q: torch.Tensor, k: int, k1: int = 0, precision="fp32", stream=None):
+        ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)
+        sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
+        lvq_search_exhaustive(self.handle, q, k1, k, precision, ids, sc, stream)
+        return ids, sc
+
+    def first_level(self, q: torch.Tensor, k1: int, precision="fp32", stream=None):
+        ids = torch.empty((q.shape[0], k1), dtype=torch.int64, device=q.device)
+        sc = torch.empty((q.shape[0], k1), dtype=torch.float32, device=q.device)
+        lvq_search_first_level(self.handle, q, k1, precision, ids, sc, stream)
+        return ids, sc
+
+    def search_candidates(self, q: torch.Tensor, cand: torch.Tensor, k: int, k1: int = 0, stream=None):
+        ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)
+        sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
+        lvq_search_candidates(self.handle, q, cand, k1, k, ids, sc, stream)
+        return ids, sc
+
+    def rerank(self, q: torch.Tensor, cand: torch.Tensor, k: int, stream=None):
+        ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)
+        sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
+        lvq_rerank(self.handle, q, cand, k, ids, sc, stream)
+        return ids, sc
+
+    def export(self, ids: torch.Tensor, stream=None):
+        n = ids.numel()
+        dev = ids.device
+        c1 = torch.empty((n, self.d), dtype=torch.uint8, device=dev)
+        c2 = torch.empty((n, self.d), dtype=torch.uint8, device=dev) if self.bits2 else None
+        lo = torch.empty(n, dtype=torch.float32, device=dev)
+        st = torch.empty(n, dtype=torch.float32, device=dev)
+        mid = torch.empty(n, dtype=torch.uint8, device=dev)
+        lvq_export(self.handle, ids, c1, c2, lo, st, mid, stream)
+        return dict(codes1=c1, codes2=c2, lower=lo, step=st, mean_id=mid)
+
+    def stats(self, stream=None) -> int:
+        return lvq_stats(self.handle, stream)
+
+    def reserve(self, max_nq: int, max_k1: int, max_cand: int = 0):
+        lvq_reserve(self.handle, max_nq, max_k1, max_cand)
+
+    def set_tuning(self, **kw):
+        lvq_set_tuning(self.handle, **kw)
+
+    def get_tuning(self) -> dict:
+        return lvq_get_tuning(self.handle)
