@@ -81,7 +81,7 @@ typedef struct lvq_store lvq_store; /* opaque; owns all of its device memory */
  * 0 means "library default". */
 typedef struct {
   int32_t mma_n;      /* queries per tcgen05 tile: 16, 32, 64 or 128 */
-  int32_t mma_splits; /* database splits per query tile (0 = fill the GPU) */
+  int32_t mma_ctas;   /* persistent CTAs of the tensor-core scan (0 = one per SM) */
   int32_t fp32_q;     /* queries per CTA of the float32 scan: 1, 2, 4, 8 or 16 */
   int32_t fp32_splits;
 } lvq_tuning;

@@ -65,6 +65,8 @@ size_t mma_scan_cand_bytes(int grid, int n_tile, int k1);
 cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& p, int n_tile,
                             const ScanPlan& plan, cudaStream_t stream);
 bool mma_supported(const DeviceStore& st);
+int mma_tile_limit(const DeviceStore& st);   // largest query tile whose queries fit in shared memory
+int mma_seg_max(int grid, int64_t groups);   // segments per query tile in the partial lists
 
 // ---- selection and re-ranking ----------------------------------------------
 // Merge the per-split lists of each query into its k1 best, then either write

@@ -81,11 +81,14 @@ int pick_qb(const lvq_store* s, int64_t nq) {
 }
 
 int pick_mma_n(const lvq_store* s, int64_t nq) {
-  if (s->tuning.mma_n > 0) return s->tuning.mma_n;
-  if (nq <= 16) return 16;
-  if (nq <= 32) return 32;
-  if (nq <= 64) return 64;
-  return 128;
+  int n;
+  if (s->tuning.mma_n > 0) n = s->tuning.mma_n;
+  else if (nq <= 16) n = 16;
+  else if (nq <= 32) n = 32;
+  else if (nq <= 64) n = 64;
+  else n = 128;
+  const int lim = mma_tile_limit(s->ds);
+  return n > lim ? lim : n;
 }
 
 // Layout of the scratch memory of a first-level scan.
@@ -127,17 +130,26 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
     groups = ceil_div(nq, sc.qb);
   }
   const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, tiles_rows);
-  int splits = mma ? s->tuning.mma_splits : s->tuning.fp32_splits;
-  if (splits <= 0) {
-    const int64_t want_items = (int64_t)grid * (mma ? 1 : 2);
-    splits = (int)ceil_div(want_items, groups);
+  int splits;
+  if (mma) {
+    // (query tile, database tile) units are shared evenly by the CTAs; a
+    // query tile is cut into at most seg_max segments
+    const int64_t units = groups * ntiles;
+    int g = s->tuning.mma_ctas > 0 ? s->tuning.mma_ctas : grid;
+    if (g > units) g = (int)units;
+    if (g < 1) g = 1;
+    sc.plan.grid = g;
+    splits = mma_seg_max(g, groups);
+  } else {
+    splits = s->tuning.fp32_splits;
+    if (splits <= 0) splits = (int)ceil_div((int64_t)grid * 2, groups);
+    if (splits > ntiles) splits = (int)ntiles;
+    if (splits < 1) splits = 1;
+    sc.plan.grid = (int)(groups * splits < grid ? groups * splits : grid);
   }
-  if (splits > ntiles) splits = (int)ntiles;
-  if (splits < 1) splits = 1;
   sc.plan.splits = splits;
   sc.plan.n_rows = n_rows;
   sc.plan.k1 = k1;
-  sc.plan.grid = (int)(groups * splits < grid ? groups * splits : grid);
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
   const size_t cand = mma ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
                           : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);
@@ -471,7 +483,7 @@ lvq_status lvq_set_tuning(lvq_store* s, const lvq_tuning* t) {
   if (t->mma_n != 0 && t->mma_n != 16 && t->mma_n != 32 && t->mma_n != 64 && t->mma_n != 128) return LVQ_EINVAL;
   if (t->fp32_q != 0 && t->fp32_q != 1 && t->fp32_q != 2 && t->fp32_q != 4 && t->fp32_q != 8 && t->fp32_q != 16)
     return LVQ_EINVAL;
-  if (t->mma_splits < 0 || t->fp32_splits < 0) return LVQ_EINVAL;
+  if (t->mma_ctas < 0 || t->fp32_splits < 0) return LVQ_EINVAL;
   std::lock_guard<std::mutex> g(s->mu);
   s->tuning = *t;
   return LVQ_OK;
