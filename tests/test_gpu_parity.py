@@ -222,7 +222,7 @@ def test_streaming_slots_match_the_replay():
         dele = np.r_[dele, dele[:5], [-1, cap + 3]]
         n_del = st.delete(torch.from_numpy(dele.astype(np.int64)).cuda())
         assert int(n_del.item()) == rep.delete(dele)
-        xn = mix.rows(0, 400 + 50 * step, stream=9, )[:, :] + np.float32(step)
+        xn = mix.rows(0, 250 + 20 * step, stream=9) + np.float32(step)
         new = st.insert(torch.from_numpy(xn).cuda())
         ref_new = rep.insert(len(xn))
         assert new.cpu().tolist() == ref_new.tolist()
