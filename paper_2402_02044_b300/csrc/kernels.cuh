@@ -32,11 +32,16 @@ cudaError_t launch_export(const DeviceStore& st, const int64_t* ids, int64_t n, 
 // ---- query preparation ------------------------------------------------------
 // Per query: qsum = sum_j q_j, qnorm = ||q||^2, cm[m] = <q, mu_m> (float32),
 // and q rounded to float16 into a zero-padded [nq_pad][kq] matrix.
+// For the tensor-core scan (q16 != null) the float16 copy of dim j is scaled
+// by 1/16 when B1 = 4 and j % 8 is 2, 3, 6 or 7 (those codes reach the tensor
+// cores as 1024 + 16c, the others as 1024 + c); q16sum = sum of the stored
+// float16 values, so that <q16, c> = acc - 1024 * q16sum.
 struct QueryPrep {
   float* qsum;      // [nq]
   float* qnorm;     // [nq]
   float* cm;        // [nq][M]
   uint16_t* q16;    // [nq_pad][kq] (may be null)
+  float* q16sum;    // [nq] (with q16)
   int64_t nq_pad;
   int kq;
 };

@@ -108,6 +108,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
   sc.prep.qnorm = c.take<float>(nq);
   sc.prep.cm = c.take<float>((size_t)nq * st.n_means);
   sc.prep.q16 = nullptr;
+  sc.prep.q16sum = nullptr;
   sc.prep.nq_pad = nq;
   sc.prep.kq = 0;
   const int64_t n_rows = s->rows_bound;
@@ -120,6 +121,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
     const int box_dims = st.bits1 == 4 ? 128 : 64;
     sc.prep.kq = (int)ceil_div(st.row1, 64) * box_dims;
     sc.prep.q16 = c.take<uint16_t>((size_t)sc.prep.nq_pad * sc.prep.kq);
+    sc.prep.q16sum = c.take<float>(nq);
     grid = s->sm_count;
     tiles_rows = 128;
     groups = sc.prep.nq_pad / sc.n_tile;
@@ -413,6 +415,7 @@ lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq
   p.qnorm = c.take<float>(nq);
   p.cm = c.take<float>((size_t)nq * st.n_means);
   p.q16 = nullptr;
+  p.q16sum = nullptr;
   p.nq_pad = nq;
   p.kq = 0;
   cudaStream_t str = (cudaStream_t)stream;

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) scan_fp32_kernel(Fp32Args a) {
   __shared__ int cnt[QB];
   __shared__ uint64_t thr[QB];
   __shared__ float qsum_s[QB];
-  __shared__ int hist[kThreads / 32][256];
+  __shared__ int hist[kThreads / 32][288];
   const DeviceStore& st = a.st;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const bool ip = st.metric == LVQ_IP;

@@ -1,13 +1,16 @@
 // First-level scan on the 5th-generation tensor cores (tcgen05), fused with
 // top-k1 selection.
 //
-// <q, x^> = <q, mu_m> + (l + off*D) sum(q) + D * <q, c - off>   (Sec. 3.2)
-// The last inner product is a [DB rows x d] . [d x queries] contraction:
-// codes minus the offset (-8..7 at 4 bits, -128..127 at 8 bits) are exact in
-// float16, the queries are rounded to float16, and the products accumulate in
-// float32 in tensor memory (TMEM).  L2 uses ||q||^2 - 2 <q, x^> + ||x^||^2.
+// <q, x^> = <q, mu_m> + l sum(q) + D <q, c>   (Sec. 3.2)
+// The last inner product is a [DB rows x d] . [d x queries] contraction run
+// on the tensor cores with float32 accumulation in tensor memory (TMEM).  A
+// code reaches them as the float16 1024 + c (4-bit codes in the upper nibble
+// of a byte as 1024 + 16c, with the matching query dims pre-scaled by 1/16):
+// OR-ing the code into the mantissa of 1024 is one LOP3 per pair of codes.
+// The queries are rounded to float16; the offset is removed afterwards,
+// <q16, c> = acc - 1024 sum(q16).  L2 uses ||q||^2 - 2 <q, x^> + ||x^||^2.
 //
-// One persistent CTA per SM, 10 warps with fixed roles:
+// One persistent CTA per SM, 14 warps with fixed roles:
 //   warp 0      TMA producer: the CTA's query tile (N queries x all dims,
 //               float16, 128-byte swizzle, resident while the CTA works on
 //               that tile) and 128-row x 64-byte boxes of codes (64-byte
@@ -15,11 +18,13 @@
 //   warp 1      allocates TMEM and issues tcgen05.mma (M = 128 database
 //               rows, N queries, K = 16) with A read from TMEM;
 //   warps 2-5   unpack: each thread owns one database row of the tile,
-//               turns 4- or 8-bit codes into centred float16 pairs and
-//               writes them with tcgen05.st into an A ring in TMEM;
-//   warps 6-9   epilogue: tcgen05.ld of the float32 accumulators (double
-//               buffered in TMEM), the affine fix-up, and the top-k1
-//               threshold filter into per-query candidate buffers.
+//               turns 4- or 8-bit codes into float16 pairs and writes them
+//               with tcgen05.st into an A ring in TMEM;
+//   warps 6-13  epilogue (two per TMEM lane quarter, each taking half of the
+//               query columns): tcgen05.ld of the float32 accumulators
+//               (double buffered in TMEM) 16 columns at a time, a cheap
+//               per-query filter, then the exact key and the top-k1
+//               threshold test for the few rows that pass it.
 // Work is the list of (query tile, database tile) units, split evenly
 // between the CTAs; a CTA's stretch of one query tile is a "segment" whose
 // k1 best keys go to partial[q][segment].
@@ -43,13 +48,16 @@ using namespace sm100;
 constexpr int kRows = 128;              // database rows per tile (MMA M)
 constexpr int kBoxBytes = 64;           // code bytes per row per TMA box
 constexpr int kStageBytes = kRows * kBoxBytes;
-constexpr int kCodeStages = 3;
-constexpr int kWarps = 10;
+constexpr int kMaxCodeStages = 16;
+constexpr int kWarps = 14;
+constexpr int kEpiWarp0 = 6;            // first of the 8 epilogue warps
+constexpr int kEpiThreads = 256;
 constexpr int kThreads = kWarps * 32;
 constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
 constexpr int kMaxQueryBytes = 196608;
+constexpr int kHistInts = 256 + 32;     // radix histogram, padded (see warp_kth)
 
 struct MmaArgs {
   DeviceStore st;
@@ -63,6 +71,7 @@ struct MmaArgs {
   int n_kbox;         // code boxes per row
   int qboxes;         // 64-dim float16 query boxes per query row
   int a_stages;       // depth of the A ring in TMEM
+  int code_stages;    // depth of the code-box ring in shared memory
   int64_t ntiles;     // database tiles
   int64_t units;      // query tiles x database tiles
   int seg_max;
@@ -74,14 +83,15 @@ struct Smem {
   int total;
 };
 
-__host__ __device__ inline Smem smem_layout(int n, int qboxes) {
+__host__ __device__ inline Smem smem_layout(int n, int qboxes, int stages) {
   Smem s;
   s.q = 0;
   s.code = qboxes * n * 128;
-  s.bars = s.code + kCodeStages * kStageBytes;
+  s.bars = s.code + stages * kStageBytes;
   s.misc = s.bars + 64 * 8;
-  // misc: tmem base (16) + abort (16) + thr[n] u64 + cnt[n] + qsum[n] + qnorm[n] + hist[4][256]
-  s.total = s.misc + 32 + n * 8 + n * 4 * 3 + 4 * 256 * 4;
+  // misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 + cnt[n] + qnorm[n] + cmax[n]
+  //       + hist[4][kHistInts]
+  s.total = s.misc + 32 + n * 8 + n * 16 + n * 4 * 3 + 4 * kHistInts * 4;
   return s;
 }
 
@@ -92,8 +102,8 @@ struct Bars {
 __device__ __forceinline__ Bars bars_at(uint64_t* b) {
   Bars r;
   r.code_full = b;
-  r.code_empty = b + kCodeStages;
-  r.a_full = b + 2 * kCodeStages;
+  r.code_empty = b + kMaxCodeStages;
+  r.a_full = b + 2 * kMaxCodeStages;
   r.a_empty = r.a_full + 8;
   r.d_full = r.a_empty + 8;
   r.d_empty = r.d_full + 2;
@@ -110,37 +120,32 @@ __device__ __forceinline__ int cta_of_unit(int64_t u, int64_t units, int grid) {
   return (int)(((u + 1) * grid - 1) / units);
 }
 
-// centred float16 pairs of one 64-byte box of a row: 4-bit -> 64 pairs, 8-bit -> 32
+// float16 pairs of one 64-byte box of a row: 4-bit -> 64 pairs, 8-bit -> 32.
+// 4-bit word (dims 8g..8g+7): the pair (2p, 2p+1) sits in bits 4p and 16+4p;
+// pairs 0 and 2 become (1024 + c, 1024 + c'), pairs 1 and 3 (1024 + 16c, ...).
 template <int BITS>
 __device__ __forceinline__ void unpack_box(const uint4 (&w)[4], uint32_t (&r)[64]) {
   if (BITS == 4) {
-    const __half2 off = __halves2half2(__float2half_rn(1032.0f), __float2half_rn(1032.0f));
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const uint32_t h = ((ws[i] >> (4 * p)) & 0x000F000Fu) | 0x64006400u;  // (1024 + c_lo, 1024 + c_hi)
-          __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&h), off);
-          r[c * 16 + i * 4 + p] = *reinterpret_cast<uint32_t*>(&v);
-        }
+        const uint32_t hi = ws[i] >> 8;
+        r[c * 16 + i * 4 + 0] = (ws[i] & 0x000F000Fu) | 0x64006400u;
+        r[c * 16 + i * 4 + 1] = (ws[i] & 0x00F000F0u) | 0x64006400u;
+        r[c * 16 + i * 4 + 2] = (hi & 0x000F000Fu) | 0x64006400u;
+        r[c * 16 + i * 4 + 3] = (hi & 0x00F000F0u) | 0x64006400u;
       }
     }
   } else {
-    const __half2 off = __halves2half2(__float2half_rn(1152.0f), __float2half_rn(1152.0f));
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const uint32_t h = __byte_perm(ws[i], 0x64646464u, p == 0 ? 0x5140 : 0x5342);  // (1024 + b, 1024 + b')
-          __half2 v = __hsub2(*reinterpret_cast<const __half2*>(&h), off);
-          r[c * 8 + i * 2 + p] = *reinterpret_cast<uint32_t*>(&v);
-        }
+        r[c * 8 + i * 2 + 0] = __byte_perm(ws[i], 0x64646464u, 0x5140);  // (1024 + b0, 1024 + b1)
+        r[c * 8 + i * 2 + 1] = __byte_perm(ws[i], 0x64646464u, 0x5342);  // (1024 + b2, 1024 + b3)
       }
     }
   }
@@ -152,10 +157,12 @@ struct Ctx {
   Bars B;
   uint32_t tbase;
   volatile int* abort_sh;
-  uint64_t* thr;
+  uint64_t* thr;    // [N] exact key threshold (insert when key < thr)
+  float4* fq;       // [N] {sum(q), 1024 sum(q16), bound, 0}: a row may enter only if its
+                    //     filter value exceeds bound
   int* cnt;
-  float* qsum_s;
   float* qnorm_s;
+  float* cmax_s;    // [N] max_m <q, mu_m>
   int* hist;
   volatile int* ep_go;  // [2] epilogue leader's verdicts, read by the 4 epilogue warps after a named barrier
   int64_t u_begin, u_end;
@@ -191,8 +198,8 @@ __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUt
     }
     for (int64_t t = t0; t < t1; ++t) {
       for (int kb = 0; kb < a.n_kbox; ++kb) {
-        const int s = ci % kCodeStages;
-        LVQ_WAIT(c, c.B.code_empty + s, ((ci / kCodeStages) & 1) ^ 1);
+        const int s = ci % a.code_stages;
+        LVQ_WAIT(c, c.B.code_empty + s, ((ci / a.code_stages) & 1) ^ 1);
         mbar_expect_tx(c.B.code_full + s, kStageBytes);
         tma_load_2d(c.cst + s * kStageBytes, cmap, c.B.code_full + s, kb * kBoxBytes, (int)(t * kRows));
         ++ci;
@@ -203,9 +210,9 @@ __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUt
 out:
   // copies that may still be in flight: the last (up to) 3 code boxes and
   // the last query tile
-  for (uint32_t j = 1; j <= (uint32_t)kCodeStages && j <= ci; ++j) {
+  for (uint32_t j = 1; j <= (uint32_t)a.code_stages && j <= ci; ++j) {
     const uint32_t k = ci - j;
-    mbar_wait(c.B.code_full + k % kCodeStages, (k / kCodeStages) & 1, kWaitLimit);
+    mbar_wait(c.B.code_full + k % a.code_stages, (k / a.code_stages) & 1, kWaitLimit);
   }
   if (qi > 0) mbar_wait(c.B.q_full, (qi - 1) & 1, kWaitLimit);
 }
@@ -239,11 +246,13 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
         LVQ_WAIT(c, c.B.a_full + s, (ai / AS) & 1);
         tc_fence_after();
         const uint32_t a_tmem = c.tbase + 2 * N + s * kACols;
+        // K step kk of this box reads query dims kg .. kg+15, kg = kb*box + 16kk:
+        // 64-dim query box kg/64 (N x 128 bytes each), byte offset 2*(kg%64)
+        const uint64_t d0 = desc_sw128(qbase + (uint32_t)(kb * kBoxDims / 64) * N * 128);
 #pragma unroll
         for (int kk = 0; kk < kKSteps; ++kk) {
-          const int kg = kb * kBoxDims + kk * 16;  // first dim of this K step
-          const uint32_t baddr = qbase + (kg >> 6) * N * 128 + (kg & 63) * 2;
-          mma_f16_ts(d_tmem, a_tmem + kk * 8, desc_sw128(baddr), kIdesc, (kb | kk) != 0);
+          const uint32_t off16 = (uint32_t)((kk * 16 / 64) * N * 128 + ((kk * 16) % 64) * 2) >> 4;
+          mma_f16_ts(d_tmem, a_tmem + kk * 8, d0 + off16, kIdesc, (kb | kk) != 0);
         }
         mma_commit(c.B.a_empty + s);
         ++ai;
@@ -268,14 +277,14 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
   const int quarter = warp & 3;
   const int row = quarter * 32 + lane;
   const uint32_t lane_base = c.tbase + ((uint32_t)(quarter * 32) << 16);
-  uint32_t ci = 0, ai = 0;
+  uint32_t ci = 0, ai = 0;  // boxes seen by the CTA so far
   for (int64_t u = c.u_begin; u < c.u_end && !*c.abort_sh;) {
     const int64_t t0 = u % a.ntiles;
     const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
     for (int64_t t = t0; t < t1; ++t) {
-      for (int kb = 0; kb < a.n_kbox; ++kb) {
-        const int s = ci % kCodeStages;
-        LVQ_WAIT(c, c.B.code_full + s, (ci / kCodeStages) & 1);
+      for (int kb = 0; kb < a.n_kbox; ++kb, ++ci, ++ai) {
+        const int s = ci % a.code_stages;
+        LVQ_WAIT(c, c.B.code_full + s, (ci / a.code_stages) & 1);
         const uint4* src = reinterpret_cast<const uint4*>(c.cst + s * kStageBytes + row * kBoxBytes);
         uint4 w[4];
         const int sw = (row >> 1) & 3;  // 64-byte swizzle of the TMA box
@@ -283,7 +292,6 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         for (int q = 0; q < 4; ++q) w[q] = src[q ^ sw];
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.code_empty + s);
-        ++ci;
         uint32_t r[64];
         unpack_box<BITS>(w, r);
         const int as = ai % AS;
@@ -296,7 +304,6 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.a_full + as);
-        ++ai;
       }
     }
     u += t1 - t0;
@@ -305,38 +312,47 @@ out:
   return;
 }
 
-template <int N>
-__device__ __forceinline__ void load_acc(uint32_t taddr, uint32_t (&v)[N]) {
-  if constexpr (N == 16) {
-    tmem_ld_x16<0>(taddr, v);
-  } else {
-    tmem_ld_x32<0>(taddr, v);
-    if constexpr (N >= 64) tmem_ld_x32<32>(taddr + 32, v);
-    if constexpr (N >= 128) {
-      tmem_ld_x32<64>(taddr + 64, v);
-      tmem_ld_x32<96>(taddr + 96, v);
-    }
-  }
+// Per-row constants of a database tile, loaded one tile ahead.
+struct RowMeta {
+  float lo, step, neg_h, nrm;
+  int m;
+  bool valid;
+};
+
+__device__ __forceinline__ RowMeta load_meta(const MmaArgs& a, int64_t rw, bool ip) {
+  RowMeta r;
+  r.valid = rw < a.n_rows && is_live(a.st.live, rw);
+  const int64_t s = r.valid ? rw : 0;
+  r.lo = __ldg(a.st.lower + s);
+  r.step = __ldg(a.st.step + s);
+  r.m = __ldg(a.st.mean_id + s);
+  r.nrm = ip ? 0.0f : __ldg(a.st.norm2 + s);
+  r.neg_h = -0.5f * r.nrm;
+  return r;
 }
 
 template <int N, int BITS>
 __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, int warp, int lane) {
   const int quarter = warp & 3;
-  const int ew = warp - 6;        // 0..3
-  const int et = ew * 32 + lane;  // 0..127
+  const int ew = warp - kEpiWarp0;  // 0..7
+  const int et = ew * 32 + lane;    // 0..255
   const int row_in = quarter * 32 + lane;
+  // columns of this warp: warps 0-3 the first half, 4-7 the second (all
+  // sixteen columns to the first set when N = 16)
+  constexpr int kHalf = N >= 32 ? N / 2 : N;
+  const int col0 = (ew >> 2) * kHalf;
+  const int col1 = col0 + kHalf <= N ? col0 + kHalf : N;
   const uint32_t lane_base = c.tbase + ((uint32_t)(quarter * 32) << 16);
   const DeviceStore& st = a.st;
   const bool ip = st.metric == LVQ_IP;
-  const float off = code_offset(BITS);
   uint64_t* mybuf = a.cand + (int64_t)c.cta * N * a.cap;
-  int* myhist = c.hist + ew * 256;
+  int* myhist = c.hist + (ew & 3) * kHistInts;
   uint32_t di = 0, pub = 0;
-  // The four epilogue warps meet at named barriers, so they must all take the
-  // same path: only warp 6 waits on mbarriers and reads the abort flag, and
-  // publishes its verdict in shared memory before a barrier.  Verdicts
-  // alternate between two slots, so a slot is rewritten only after every
-  // warp has passed the barrier that follows its read.
+  // The eight epilogue warps meet at named barriers, so they must all take
+  // the same path: only the first waits on mbarriers and reads the abort
+  // flag, and publishes its verdict in shared memory before a barrier.
+  // Verdicts alternate between two slots, so a slot is rewritten only after
+  // every warp has passed the barrier that follows its read.
   for (int64_t u = c.u_begin; u < c.u_end;) {
     const int64_t g = u / a.ntiles, t0 = u % a.ntiles;
     const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
@@ -345,12 +361,19 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       const bool real = q0 + et < a.nq;
       c.thr[et] = real ? kNoKey : 0ull;
       c.cnt[et] = 0;
-      c.qsum_s[et] = real ? a.p.qsum[q0 + et] : 0.0f;
+      float cmax = __int_as_float(0xff800000);
+      if (real)
+        for (int m = 0; m < st.n_means; ++m) cmax = fmaxf(cmax, a.p.cm[(q0 + et) * st.n_means + m]);
+      c.cmax_s[et] = real ? cmax : 0.0f;
       c.qnorm_s[et] = real ? a.p.qnorm[q0 + et] : 0.0f;
+      // absent queries take nothing (bound +inf), real ones everything (-inf)
+      c.fq[et] = make_float4(real ? a.p.qsum[q0 + et] : 0.0f, real ? 1024.0f * a.p.q16sum[q0 + et] : 0.0f,
+                             real ? __int_as_float(0xff800000) : __int_as_float(0x7f800000), 0.0f);
     }
     if (et == 0) c.ep_go[pub & 1] = !*c.abort_sh;
-    named_bar(1, 128);
+    named_bar(1, kEpiThreads);
     if (!c.ep_go[pub++ & 1]) goto out;
+    RowMeta nxt = load_meta(a, t0 * kRows + row_in, ip);
     for (int64_t t = t0; t < t1; ++t) {
       const int db = di & 1;
       if (ew == 0) {
@@ -362,48 +385,77 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
         __syncwarp();
         if (lane == 0) c.ep_go[pub & 1] = ok;
       }
-      named_bar(1, 128);
+      named_bar(1, kEpiThreads);
       if (!c.ep_go[pub++ & 1]) goto out;
       tc_fence_after();
-      uint32_t v[N];
-      load_acc<N>(lane_base + db * N, v);
-      tmem_ld_wait();
+      const RowMeta cur = nxt;
+      if (t + 1 < t1) nxt = load_meta(a, (t + 1) * kRows + row_in, ip);
+      const int64_t rw = t * kRows + row_in;
+      const float* cm_row = a.p.cm + q0 * st.n_means + cur.m;
+      // Filter value: D <q16, c> + l sum(q) - ||x^||^2 / 2 (IP: no norm term).
+      // A row can beat the query's threshold only if it exceeds fq[n].z, a
+      // bound built with max_m <q, mu_m>; the rows that pass get their exact
+      // key (their <q, mu_m> loads issued together) and the exact test.
+#pragma unroll 1
+      for (int c0 = col0; c0 < col1; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld_x16<0>(lane_base + db * N + c0, v);
+        tmem_ld_wait();
+        uint32_t pass = 0;
+        float acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float4 f = c.fq[c0 + j];
+          acc[j] = __uint_as_float(v[j]) - f.y;
+          const float fv = __fmaf_rn(cur.lo, f.x, __fmaf_rn(cur.step, acc[j], cur.neg_h));
+          pass |= (fv > f.z ? 1u : 0u) << j;
+        }
+        if (!cur.valid) pass = 0;
+        if (__any_sync(kFull, pass != 0)) {
+          float cmv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            cmv[j] = ((pass >> j) & 1u) ? __ldg(cm_row + (c0 + j) * st.n_means) : 0.0f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if ((pass >> j) & 1u) {
+              const int n = c0 + j;
+              float sc = __fmaf_rn(cur.step, acc[j], __fmaf_rn(cur.lo, c.fq[n].x, cmv[j]));
+              if (!ip) sc = c.qnorm_s[n] + cur.nrm - 2.0f * sc;
+              const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
+              if (key < c.thr[n]) mybuf[n * a.cap + atomicAdd(&c.cnt[n], 1)] = key;
+            }
+          }
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(c.B.d_empty + db);
       ++di;
-      const int64_t rw = t * kRows + row_in;
-      if (rw < a.n_rows && is_live(st.live, rw)) {
-        const float lo = __ldg(st.lower + rw), step = __ldg(st.step + rw);
-        const int m = __ldg(st.mean_id + rw);
-        const float nrm = ip ? 0.0f : __ldg(st.norm2 + rw);
-        const float base_ip = __fmaf_rn(off, step, lo);
-        const float* cmq = a.p.cm + q0 * st.n_means + m;
-#pragma unroll
-        for (int n = 0; n < N; ++n) {
-          if (q0 + n < a.nq) {
-            const float acc = __uint_as_float(v[n]);
-            float s = __fmaf_rn(step, acc, __fmaf_rn(base_ip, c.qsum_s[n], __ldg(cmq + n * st.n_means)));
-            if (!ip) s = c.qnorm_s[n] + nrm - 2.0f * s;
-            const uint64_t key = make_key(s, (uint32_t)rw, st.metric);
-            if (key < c.thr[n]) mybuf[n * a.cap + atomicAdd(&c.cnt[n], 1)] = key;
+      named_bar(1, kEpiThreads);
+      if (ew < 4) {
+        for (int n = ew; n < N; n += 4) {
+          if (c.cnt[n] > a.cap - kRows) {
+            uint64_t tk;
+            const int kept = warp_select_small(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
+            if (lane == 0) {
+              c.cnt[n] = kept;
+              c.thr[n] = tk;
+              if (tk != kNoKey) {
+                // the new threshold score, turned into a bound on the filter value
+                const float ts = key_score(tk, st.metric);
+                const float cm = c.cmax_s[n];
+                float b = ip ? ts - cm : 0.5f * (c.qnorm_s[n] - ts) - cm;
+                b -= 1e-5f * (fabsf(ts) + fabsf(cm) + c.qnorm_s[n]) + 1e-30f;
+                c.fq[n].z = b;
+              }
+            }
           }
         }
       }
-      named_bar(1, 128);
-      for (int n = ew; n < N; n += 4) {
-        if (c.cnt[n] > a.cap - kRows) {
-          uint64_t tk;
-          const int kept = warp_select(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
-          if (lane == 0) {
-            c.cnt[n] = kept;
-            c.thr[n] = tk;
-          }
-        }
-      }
-      named_bar(1, 128);
+      named_bar(1, kEpiThreads);
     }
-    {
+    if (ew < 4) {
       // end of this CTA's segment of query tile g: k1 best of each query
       const int seg = c.cta - cta_of_unit(g * a.ntiles, a.units, c.grid);
       if (seg < 0 || seg >= a.seg_max) {
@@ -412,13 +464,13 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
         for (int n = ew; n < N; n += 4) {
           if (q0 + n >= a.nq) continue;
           uint64_t tk;
-          const int kept = warp_select(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
+          const int kept = warp_select_small(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
           uint64_t* dst = a.partial + ((q0 + n) * a.seg_max + seg) * a.k1;
           for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? mybuf[n * a.cap + i] : kNoKey;
         }
       }
     }
-    named_bar(1, 128);
+    named_bar(1, kEpiThreads);
     u += t1 - t0;
   }
 out:
@@ -433,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const Smem L = smem_layout(N, a.qboxes);
+  const Smem L = smem_layout(N, a.qboxes, a.code_stages);
   Ctx c;
   c.qs = smem + L.q;
   c.cst = smem + L.code;
@@ -441,10 +493,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_base_sh = reinterpret_cast<uint32_t*>(smem + L.misc);
   c.abort_sh = reinterpret_cast<volatile int*>(smem + L.misc + 16);
   c.thr = reinterpret_cast<uint64_t*>(smem + L.misc + 32);
-  c.cnt = reinterpret_cast<int*>(c.thr + N);
-  c.qsum_s = reinterpret_cast<float*>(c.cnt + N);
-  c.qnorm_s = c.qsum_s + N;
-  c.hist = reinterpret_cast<int*>(c.qnorm_s + N);
+  c.fq = reinterpret_cast<float4*>(c.thr + N);
+  c.cnt = reinterpret_cast<int*>(c.fq + N);
+  c.qnorm_s = reinterpret_cast<float*>(c.cnt + N);
+  c.cmax_s = c.qnorm_s + N;
+  c.hist = reinterpret_cast<int*>(c.cmax_s + N);
   c.ep_go = reinterpret_cast<volatile int*>(smem + L.misc + 20);  // two ints
   c.B = bars_at(bar_mem);
   c.grid = gridDim.x;
@@ -454,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kCodeStages; ++i) {
+    for (int i = 0; i < a.code_stages; ++i) {
       mbar_init(c.B.code_full + i, 1);
       mbar_init(c.B.code_empty + i, 4);
     }
@@ -464,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(c.B.d_full + i, 1);
-      mbar_init(c.B.d_empty + i, 4);
+      mbar_init(c.B.d_empty + i, 8);
     }
     mbar_init(c.B.q_full, 1);
     mbar_init(c.B.q_empty, 1);
@@ -486,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) producer_role<N, BITS>(&cmap, &qmap, a, c);
   } else if (warp == 1) {
     if (lane == 0) mma_role<N, BITS>(a, c);
-  } else if (warp < 6) {
+  } else if (warp < kEpiWarp0) {
     unpack_role<N, BITS>(a, c, warp, lane);
   } else {
     epilogue_role<N, BITS>(a, c, warp, lane);
@@ -512,6 +565,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }
   return fn;
+}
+
+// candidate buffer per (CTA, query): room for k1 kept keys, a tile of new
+// ones, and slack so that compactions are rare; at most 1024 keys (the
+// radix select holds them in registers)
+int mma_cap(int k1) {
+  const int c = 2 * pow2_at_least(k1 + kRows);
+  return c <= 1024 ? c : 1024;
 }
 
 int max_n_tile(const DeviceStore& st) {
@@ -543,9 +604,7 @@ bool mma_supported(const DeviceStore& st) {
 
 int mma_tile_limit(const DeviceStore& st) { return max_n_tile(st); }
 
-size_t mma_scan_cand_bytes(int grid, int n_tile, int k1) {
-  return (size_t)grid * n_tile * pow2_at_least(k1 + kRows) * 8;
-}
+size_t mma_scan_cand_bytes(int grid, int n_tile, int k1) { return (size_t)grid * n_tile * mma_cap(k1) * 8; }
 
 int mma_seg_max(int grid, int64_t groups) { return (int)ceil_div(grid, groups) + 1; }
 
@@ -563,7 +622,7 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   a.n_rows = plan.n_rows;
   a.partial = plan.partial;
   a.cand = plan.cand;
-  a.cap = pow2_at_least(plan.k1 + kRows);
+  a.cap = mma_cap(plan.k1);
   a.n_kbox = (int)ceil_div(st.row1, kBoxBytes);
   a.qboxes = qboxes;
   const int acols = st.bits1 == 4 ? 64 : 32;
@@ -598,7 +657,12 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   }
   cudaError_t e = cudaMemsetAsync(plan.partial, 0xFF, (size_t)nq * a.seg_max * plan.k1 * 8, stream);
   if (e != cudaSuccess) return e;
-  const Smem L = smem_layout(n_tile, qboxes);
+  // as many code stages as shared memory allows (more bytes in flight for
+  // narrow query tiles)
+  a.code_stages = kMaxCodeStages;
+  while (a.code_stages > 2 && (size_t)smem_layout(n_tile, qboxes, a.code_stages).total + 1024 > 232448)
+    --a.code_stages;
+  const Smem L = smem_layout(n_tile, qboxes, a.code_stages);
   size_t smem = (size_t)L.total + 1024;
   if (smem < (size_t)kMinSmem) smem = kMinSmem;
   if (smem > 232448) return cudaErrorInvalidConfiguration;

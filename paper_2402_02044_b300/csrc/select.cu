@@ -19,8 +19,16 @@ __global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* 
     const bool real = i < nq;
     if (p.q16) {
       __half* dst = reinterpret_cast<__half*>(p.q16) + i * p.kq;
-      for (int j = lane; j < p.kq; j += 32)
-        dst[j] = (real && j < d) ? __float2half_rn(q[i * d + j]) : __float2half_rn(0.0f);
+      float hs = 0.0f;
+      for (int j = lane; j < p.kq; j += 32) {
+        float v = (real && j < d) ? q[i * d + j] : 0.0f;
+        if (st.bits1 == 4 && (j & 2)) v *= 0.0625f;  // j % 8 in {2, 3, 6, 7}
+        const __half h = __float2half_rn(v);
+        dst[j] = h;
+        hs += __half2float(h);
+      }
+      hs = warp_sum(hs);
+      if (real && lane == 0) p.q16sum[i] = hs;
     }
     if (!real) continue;
     const float* qi = q + i * d;
@@ -84,7 +92,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore
   int* sh_pos = reinterpret_cast<int*>(qsh + st.d);
   __shared__ int cnt;
   __shared__ uint64_t thr;
-  __shared__ int hist[256];
+  __shared__ int hist[288];
   if (threadIdx.x == 0) {
     cnt = 0;
     thr = kNoKey;

@@ -20,23 +20,32 @@ __host__ __device__ inline int pow2_at_least(int v) {
   return p;
 }
 
-// k-th smallest (1-based, 1 <= k <= n) of the n distinct keys buf[0..n),
-// found by one whole warp.  hist: 256 ints of shared memory owned by the warp.
-__device__ __forceinline__ uint64_t warp_kth(const uint64_t* buf, int n, int k, int* hist) {
+// Radix select on keys held in registers: key i of the warp's n keys is
+// v[i / 32] of lane i % 32 (E registers per lane, n <= 32 * E; entries at
+// or beyond n hold kNoKey and are never counted).  Returns the k-th smallest
+// (1-based, 1 <= k <= n) of the n distinct keys, using 8-bit digits from the
+// most significant one and a 256-bin histogram in shared memory.  hist: 288
+// ints owned by the warp; bin b lives at b + b/8 so that lane l reading its
+// bins 8l..8l+7 touches banks 9l..9l+7 (mod 32): no bank conflicts.
+template <int E>
+__device__ __forceinline__ uint64_t warp_kth_regs(const uint64_t (&v)[E], int n, int k, int* hist) {
   const int lane = threadIdx.x & 31;
   uint64_t prefix = 0, mask = 0;
   for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    for (int i = lane; i < 288; i += 32) hist[i] = 0;
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const uint64_t key = buf[i];
-      if ((key & mask) == prefix) atomicAdd(&hist[(int)((key >> shift) & 255u)], 1);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (e * 32 + lane < n && (v[e] & mask) == prefix) {
+        const int b = (int)((v[e] >> shift) & 255u);
+        atomicAdd(&hist[b + (b >> 3)], 1);
+      }
     }
     __syncwarp();
     int c[8], s = 0;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      c[e] = hist[lane * 8 + e];
+      c[e] = hist[lane * 9 + e];
       s += c[e];
     }
     int incl = s;
@@ -70,14 +79,10 @@ __device__ __forceinline__ uint64_t warp_kth(const uint64_t* buf, int n, int k, 
     __syncwarp();
     if (inbin == 1) {
       // a single key carries this prefix: it is the answer
-      uint64_t found = 0;
-      for (int i = lane; i < n; i += 32) {
-        const uint64_t key = buf[i];
-        if ((key & mask) == prefix) found = key;
-      }
-      // the matching key is the only candidate that is not 0 (a key of 0
-      // would equal the prefix, which is then returned all the same)
-      uint64_t r = found;
+      uint64_t r = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e * 32 + lane < n && (v[e] & mask) == prefix) r = v[e];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const uint64_t y = __shfl_xor_sync(kFull, r, o);
@@ -91,15 +96,97 @@ __device__ __forceinline__ uint64_t warp_kth(const uint64_t* buf, int n, int k, 
 
 // Keep the k smallest of the n distinct keys buf[0..n) at buf[0..kept),
 // unsorted; returns kept = min(n, k) and sets *thr to the k-th smallest key
-// when n >= k (else kNoKey).  One whole warp.
-__device__ __forceinline__ int warp_select(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+// when n >= k (else kNoKey).  One whole warp; n <= 32 * E.
+template <int E>
+__device__ __forceinline__ int warp_select_e(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
   const int lane = threadIdx.x & 31;
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = e * 32 + lane < n ? buf[e * 32 + lane] : kNoKey;
   if (n <= k) {
-    *thr = (n == k && k > 0) ? warp_kth(buf, n, k, hist) : kNoKey;
+    *thr = (n == k && k > 0) ? warp_kth_regs<E>(v, n, k, hist) : kNoKey;
     __syncwarp();
     return n;
   }
-  const uint64_t t = warp_kth(buf, n, k, hist);
+  const uint64_t t = warp_kth_regs<E>(v, n, k, hist);
+  int pos = 0;
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const bool keep = e * 32 + lane < n && v[e] <= t;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = v[e];
+    pos += __popc(bal);
+  }
+  __syncwarp();
+  *thr = t;
+  return pos;
+}
+
+// k-th smallest of the n distinct keys buf[0..n) by the same radix select,
+// reading the keys from memory on every pass (no registers held; for large
+// buffers in register-bound kernels).
+__device__ __forceinline__ uint64_t warp_kth_mem(const uint64_t* buf, int n, int k, int* hist) {
+  const int lane = threadIdx.x & 31;
+  uint64_t prefix = 0, mask = 0;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = lane; i < 288; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint64_t key = buf[i];
+      if ((key & mask) == prefix) {
+        const int b = (int)((key >> shift) & 255u);
+        atomicAdd(&hist[b + (b >> 3)], 1);
+      }
+    }
+    __syncwarp();
+    int c[8], s = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      c[e] = hist[lane * 9 + e];
+      s += c[e];
+    }
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - s;
+    const bool mine = excl < k && k <= incl;
+    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+    int bin = 0, before = 0;
+    if (mine) {
+      int run = excl;
+      bool found = false;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        if (!found && run < k && k <= run + c[e]) {
+          bin = lane * 8 + e;
+          before = run;
+          found = true;
+        }
+        run += c[e];
+      }
+    }
+    bin = __shfl_sync(kFull, bin, src);
+    before = __shfl_sync(kFull, before, src);
+    k -= before;
+    prefix |= (uint64_t)bin << shift;
+    mask |= 255ull << shift;
+    __syncwarp();
+  }
+  return prefix;
+}
+
+__device__ __forceinline__ int warp_select_mem(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  const int lane = threadIdx.x & 31;
+  if (n <= k) {
+    *thr = (n == k && k > 0) ? warp_kth_mem(buf, n, k, hist) : kNoKey;
+    __syncwarp();
+    return n;
+  }
+  const uint64_t t = warp_kth_mem(buf, n, k, hist);
   int pos = 0;
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
@@ -113,6 +200,20 @@ __device__ __forceinline__ int warp_select(uint64_t* buf, int n, int k, int* his
   }
   *thr = t;
   return pos;
+}
+
+// Up to 512 keys in registers, more from memory (for register-bound kernels).
+__device__ __forceinline__ int warp_select_small(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  if (n <= 256) return warp_select_e<8>(buf, n, k, hist, thr);
+  if (n <= 512) return warp_select_e<16>(buf, n, k, hist, thr);
+  return warp_select_mem(buf, n, k, hist, thr);
+}
+
+// Runtime dispatch on the number of keys (held in registers); n <= 1024.
+__device__ __forceinline__ int warp_select(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  if (n <= 256) return warp_select_e<8>(buf, n, k, hist, thr);
+  if (n <= 512) return warp_select_e<16>(buf, n, k, hist, thr);
+  return warp_select_e<32>(buf, n, k, hist, thr);
 }
 
 // Ascending bitonic sort of keys[0..n) in shared memory, n a power of two;
