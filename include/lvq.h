@@ -93,8 +93,15 @@ typedef struct {
  * Errors: LVQ_EINVAL for a bad config, LVQ_ENOMEM, LVQ_ECUDA. */
 lvq_status lvq_create(const lvq_config *cfg, const float *means_host, lvq_store **out);
 
-/* Free the store and all of its device memory.  Synchronises the device. */
+/* Free the store and all of its device memory (a view: its scratch memory
+ * only).  Synchronises the device.  Destroy a store's views before it. */
 lvq_status lvq_destroy(lvq_store *store);
+
+/* A second handle on the same store: it shares the vectors, slots and
+ * counters of `base` but has its own scratch memory, tile shapes and timing,
+ * so searches through different views may run concurrently on different
+ * streams.  Updates through any handle act on the shared store. */
+lvq_status lvq_store_view(const lvq_store *base, lvq_store **out);
 
 /* Encode n vectors without touching the store (Eq. 1-3, Def. 1, Sec. 2.2).
  * x: n x d float32, row-major.
@@ -119,6 +126,17 @@ lvq_status lvq_encode(const lvq_store *store, const float *x, int64_t n, uint8_t
  * out_ids is filled with -1 and LVQ_EFULL is recorded (sticky). */
 lvq_status lvq_insert(lvq_store *store, const float *x, int64_t n, int64_t *out_ids,
                       lvq_stream_t stream);
+
+/* Deferred insert: like lvq_insert (same slot choice, encoding and errors)
+ * but the slots stay invisible to searches, and unavailable to other inserts,
+ * until lvq_publish.  A serving loop encodes new vectors while searches run
+ * and publishes them between batches. */
+lvq_status lvq_insert_deferred(lvq_store *store, const float *x, int64_t n, int64_t *out_ids,
+                               lvq_stream_t stream);
+
+/* Make slots written by lvq_insert_deferred visible.  ids: n int64; ids that
+ * are out of range or not pending are ignored. */
+lvq_status lvq_publish(lvq_store *store, const int64_t *ids, int64_t n, lvq_stream_t stream);
 
 /* Delete slots (Sec. 2.1: X_t = X_{t-1} - {x}; lazy, App. A.2): from the
  * stream position of the call on, the slots are excluded from every result

@@ -206,21 +206,23 @@ constexpr int kAllocThreads = 256;
 constexpr int kAllocWordsPerThread = 4;
 constexpr int kAllocWordsPerBlock = kAllocThreads * kAllocWordsPerThread;
 
-__device__ __forceinline__ uint32_t free_mask(const uint32_t* live, int64_t w, int64_t capacity) {
+__device__ __forceinline__ uint32_t free_mask(const uint32_t* live, const uint32_t* reserved, int64_t w,
+                                              int64_t capacity) {
   const int64_t base = w * 32;
   if (base >= capacity) return 0u;
   uint32_t valid = (capacity - base >= 32) ? 0xffffffffu : ((1u << (capacity - base)) - 1u);
-  return ~live[w] & valid;
+  return ~(live[w] | reserved[w]) & valid;
 }
 
-__global__ void __launch_bounds__(kAllocThreads) free_count_kernel(const uint32_t* live, int64_t capacity,
-                                                                   int64_t nwords, int32_t* block_free) {
+__global__ void __launch_bounds__(kAllocThreads) free_count_kernel(const uint32_t* live, const uint32_t* reserved,
+                                                                   int64_t capacity, int64_t nwords,
+                                                                   int32_t* block_free) {
   __shared__ int sh[kAllocThreads / 32];
   int cnt = 0;
   const int64_t w0 = (int64_t)blockIdx.x * kAllocWordsPerBlock + threadIdx.x * kAllocWordsPerThread;
 #pragma unroll
   for (int i = 0; i < kAllocWordsPerThread; ++i)
-    if (w0 + i < nwords) cnt += __popc(free_mask(live, w0 + i, capacity));
+    if (w0 + i < nwords) cnt += __popc(free_mask(live, reserved, w0 + i, capacity));
   int total;
   block_exclusive_scan(cnt, sh, total);
   if (threadIdx.x == 0) block_free[blockIdx.x] = total;
@@ -255,7 +257,8 @@ __global__ void __launch_bounds__(1024) alloc_scan_kernel(int32_t* block_free, i
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) out_ids[i] = -1;
 }
 
-__global__ void __launch_bounds__(kAllocThreads) alloc_assign_kernel(const uint32_t* live, int64_t capacity,
+__global__ void __launch_bounds__(kAllocThreads) alloc_assign_kernel(const uint32_t* live, const uint32_t* reserved,
+                                                                     int64_t capacity,
                                                                      int64_t nwords, const int32_t* block_base,
                                                                      int64_t n, const int32_t* abort_flag,
                                                                      int64_t* out_ids) {
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_assign_kernel(const uint3
   int cnt = 0;
 #pragma unroll
   for (int i = 0; i < kAllocWordsPerThread; ++i) {
-    masks[i] = (w0 + i < nwords) ? free_mask(live, w0 + i, capacity) : 0u;
+    masks[i] = (w0 + i < nwords) ? free_mask(live, reserved, w0 + i, capacity) : 0u;
     cnt += __popc(masks[i]);
   }
   int total;
@@ -284,14 +287,34 @@ __global__ void __launch_bounds__(kAllocThreads) alloc_assign_kernel(const uint3
   }
 }
 
-__global__ void publish_kernel(uint32_t* live, const int64_t* ids, int64_t n, const int32_t* abort_flag,
-                               int64_t* n_live) {
+// mode 0: make the freshly inserted slots live; mode 1: mark them reserved
+// (deferred insert).  Skipped when the allocation was abandoned.
+__global__ void publish_kernel(uint32_t* live, uint32_t* reserved, const int64_t* ids, int64_t n,
+                               const int32_t* abort_flag, int64_t* n_live, int mode) {
   if (*abort_flag) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = ids[i];
-    atomicOr(live + (s >> 5), 1u << (s & 31));
+    atomicOr((mode == 0 ? live : reserved) + (s >> 5), 1u << (s & 31));
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(n_live), (unsigned long long)n);
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(n_live), (unsigned long long)n);
+}
+
+// Publication of deferred inserts: reserved slots become live.  Ids that are
+// out of range or not reserved are ignored; the count of newly live slots is
+// added to n_live.
+__global__ void publish_reserved_kernel(uint32_t* live, uint32_t* reserved, int64_t capacity, const int64_t* ids,
+                                        int64_t n, int64_t* n_live) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = ids[i];
+    if (s < 0 || s >= capacity) continue;
+    const uint32_t bit = 1u << (s & 31);
+    const uint32_t old = atomicAnd(reserved + (s >> 5), ~bit);
+    if (old & bit) {
+      atomicOr(live + (s >> 5), bit);
+      atomicAdd(reinterpret_cast<unsigned long long*>(n_live), 1ull);
+    }
+  }
 }
 
 __global__ void delete_kernel(uint32_t* live, int64_t capacity, const int64_t* ids, int64_t n,
@@ -381,17 +404,26 @@ cudaError_t launch_alloc_slots(const DeviceStore& st, int64_t n, int64_t* out_id
                                int32_t* abort_flag, cudaStream_t stream) {
   const int64_t nwords = ceil_div(st.capacity, 32);
   const int nblocks = (int)ceil_div(nwords, kAllocWordsPerBlock);
-  free_count_kernel<<<nblocks, kAllocThreads, 0, stream>>>(st.live, st.capacity, nwords, scratch);
+  free_count_kernel<<<nblocks, kAllocThreads, 0, stream>>>(st.live, st.reserved, st.capacity, nwords, scratch);
   alloc_scan_kernel<<<1, 1024, 0, stream>>>(scratch, nblocks, n, abort_flag, st.err, out_ids);
-  alloc_assign_kernel<<<nblocks, kAllocThreads, 0, stream>>>(st.live, st.capacity, nwords, scratch, n,
+  alloc_assign_kernel<<<nblocks, kAllocThreads, 0, stream>>>(st.live, st.reserved, st.capacity, nwords, scratch, n,
                                                             abort_flag, out_ids);
   return cudaGetLastError();
 }
 
 cudaError_t launch_publish(const DeviceStore& st, const int64_t* ids, int64_t n, const int32_t* abort_flag,
-                           int64_t* n_live, cudaStream_t stream) {
+                           int64_t* n_live, bool deferred, cudaStream_t stream) {
   const int blocks = (int)(ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096);
-  publish_kernel<<<blocks > 0 ? blocks : 1, 256, 0, stream>>>(st.live, ids, n, abort_flag, n_live);
+  publish_kernel<<<blocks > 0 ? blocks : 1, 256, 0, stream>>>(st.live, st.reserved, ids, n, abort_flag, n_live,
+                                                              deferred ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_publish_reserved(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* n_live,
+                                    cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)(ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096);
+  publish_reserved_kernel<<<blocks, 256, 0, stream>>>(st.live, st.reserved, st.capacity, ids, n, n_live);
   return cudaGetLastError();
 }
 

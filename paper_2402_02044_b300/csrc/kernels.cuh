@@ -23,7 +23,9 @@ size_t alloc_scratch_bytes(int64_t capacity);
 cudaError_t launch_alloc_slots(const DeviceStore& st, int64_t n, int64_t* out_ids, int32_t* scratch,
                                int32_t* abort_flag, cudaStream_t stream);
 cudaError_t launch_publish(const DeviceStore& st, const int64_t* ids, int64_t n, const int32_t* abort_flag,
-                           int64_t* n_live, cudaStream_t stream);
+                           int64_t* n_live, bool deferred, cudaStream_t stream);
+cudaError_t launch_publish_reserved(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* n_live,
+                                    cudaStream_t stream);
 cudaError_t launch_delete(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* out_n,
                           unsigned long long* count, int64_t* n_live, cudaStream_t stream);
 cudaError_t launch_export(const DeviceStore& st, const int64_t* ids, int64_t n, uint8_t* codes1,

@@ -67,6 +67,8 @@ lvq_status ensure_ws(lvq_store* s, size_t bytes) {
   return LVQ_OK;
 }
 
+lvq_store* root_of(const lvq_store* s) { return const_cast<lvq_store*>(s->base ? s->base : s); }
+
 bool valid_stream_device(const lvq_store* s) {
   int dev = -1;
   return cudaGetDevice(&dev) == cudaSuccess && dev == s->device;
@@ -111,7 +113,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
   sc.prep.q16sum = nullptr;
   sc.prep.nq_pad = nq;
   sc.prep.kq = 0;
-  const int64_t n_rows = s->rows_bound;
+  const int64_t n_rows = root_of(s)->rows_bound.load();
   int grid, tiles_rows;
   int64_t groups;
   if (mma) {
@@ -254,7 +256,6 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   lvq_store* s = new (std::nothrow) lvq_store();
   if (!s) return LVQ_ENOMEM;
   s->cfg = *cfg;
-  s->rows_bound = 0;
   memset(&s->tuning, 0, sizeof(s->tuning));
   DeviceStore& st = s->ds;
   memset(&st, 0, sizeof(st));
@@ -279,10 +280,12 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   A((void**)&st.norm2, (size_t)cap * 4);
   A((void**)&st.mean_id, (size_t)round_up(cap, 16));
   A((void**)&st.live, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
+  A((void**)&st.reserved, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
   A((void**)&st.means, (size_t)cfg->n_means * cfg->d * 4);
   A((void**)&st.err, 16);
   A((void**)&s->counters, kCtrWords * 8 + alloc_scratch_bytes(cap));
   if (e == cudaSuccess) e = cudaMemset(st.live, 0, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
+  if (e == cudaSuccess) e = cudaMemset(st.reserved, 0, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
   if (e == cudaSuccess) e = cudaMemset(st.err, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(s->counters, 0, kCtrWords * 8);
   if (e == cudaSuccess) e = cudaMemset(st.codes1, 0, (size_t)cap * st.row1);
@@ -300,12 +303,38 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
 lvq_status lvq_destroy(lvq_store* s) {
   if (!s) return LVQ_EINVAL;
   cudaDeviceSynchronize();
+  for (auto& r : s->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (s->base) {  // a view owns only its scratch memory
+    if (s->ws) cudaFree(s->ws);
+    delete s;
+    return LVQ_OK;
+  }
   DeviceStore& st = s->ds;
-  void* ptrs[] = {st.codes1, st.codes2, st.lower, st.step, st.norm2, st.mean_id, st.live, st.means, st.err,
-                  s->counters, s->ws};
+  void* ptrs[] = {st.codes1, st.codes2,  st.lower, st.step,     st.norm2, st.mean_id,
+                  st.live,   st.reserved, st.means, st.err,     s->counters, s->ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete s;
+  return LVQ_OK;
+}
+
+lvq_status lvq_store_view(const lvq_store* base, lvq_store** out) {
+  if (!base || !out) return LVQ_EINVAL;
+  *out = nullptr;
+  lvq_store* b = root_of(base);
+  lvq_store* v = new (std::nothrow) lvq_store();
+  if (!v) return LVQ_ENOMEM;
+  v->cfg = b->cfg;
+  v->device = b->device;
+  v->ds = b->ds;
+  v->base = b;
+  v->counters = b->counters;
+  v->sm_count = b->sm_count;
+  memset(&v->tuning, 0, sizeof(v->tuning));
+  *out = v;
   return LVQ_OK;
 }
 
@@ -327,14 +356,16 @@ lvq_status lvq_encode(const lvq_store* s, const float* x, int64_t n, uint8_t* co
   return LVQ_OK;
 }
 
-lvq_status lvq_insert(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream) {
+static lvq_status insert_impl(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream,
+                              bool deferred) {
   if (!s) return LVQ_EINVAL;
   if (n < 0 || n > s->ds.capacity) return fail(s, LVQ_EINVAL, "n out of range");
   if (n == 0) return LVQ_OK;
   if (!x || !out_ids) return fail(s, LVQ_EINVAL, "null pointer");
   if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  lvq_store* r = root_of(s);
   cudaStream_t st = (cudaStream_t)stream;
-  int64_t* ctr = s->counters;
+  int64_t* ctr = r->counters;
   int32_t* abort_flag = reinterpret_cast<int32_t*>(ctr + kCtrAbort);
   int32_t* scratch = reinterpret_cast<int32_t*>(ctr + kCtrWords);
   {
@@ -344,10 +375,34 @@ lvq_status lvq_insert(lvq_store* s, const float* x, int64_t n, int64_t* out_ids,
     o.slots = out_ids;
     o.abort_flag = abort_flag;
     LVQ_CUDA(s, launch_encode(s->ds, x, n, o, st), "encode(insert)");
-    LVQ_CUDA(s, launch_publish(s->ds, out_ids, n, abort_flag, ctr + kCtrLive, st), "publish");
+    LVQ_CUDA(s, launch_publish(s->ds, out_ids, n, abort_flag, ctr + kCtrLive, deferred, st), "publish");
   }
-  std::lock_guard<std::mutex> g(s->mu);
-  s->rows_bound = s->rows_bound + n < s->ds.capacity ? s->rows_bound + n : s->ds.capacity;
+  // the n lowest free slots lie below (live + reserved + n) <= bound + n
+  int64_t cur = r->rows_bound.load();
+  int64_t nxt;
+  do {
+    nxt = cur + n < s->ds.capacity ? cur + n : s->ds.capacity;
+  } while (!r->rows_bound.compare_exchange_weak(cur, nxt));
+  return LVQ_OK;
+}
+
+lvq_status lvq_insert(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream) {
+  return insert_impl(s, x, n, out_ids, stream, false);
+}
+
+lvq_status lvq_insert_deferred(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream) {
+  return insert_impl(s, x, n, out_ids, stream, true);
+}
+
+lvq_status lvq_publish(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (n == 0) return LVQ_OK;
+  if (!ids) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  Prof p(s, (cudaStream_t)stream, LVQ_K_INSERT);
+  LVQ_CUDA(s, launch_publish_reserved(s->ds, ids, n, root_of(s)->counters + kCtrLive, (cudaStream_t)stream),
+           "publish_reserved");
   return LVQ_OK;
 }
 
@@ -356,7 +411,7 @@ lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (!out_n_deleted || (n > 0 && !ids)) return fail(s, LVQ_EINVAL, "null pointer");
   if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
-  int64_t* ctr = s->counters;
+  int64_t* ctr = root_of(s)->counters;
   Prof p(s, (cudaStream_t)stream, LVQ_K_DELETE, n > 0 ? 2 : 1);
   LVQ_CUDA(s,
            launch_delete(s->ds, ids, n, out_n_deleted, reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount),
@@ -459,7 +514,7 @@ lvq_status lvq_stats(const lvq_store* s, int64_t* n_live_host, lvq_stream_t stre
   LVQ_CUDA(s, cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
   int64_t live = 0;
   int32_t err = 0;
-  LVQ_CUDA(s, cudaMemcpy(&live, s->counters + kCtrLive, 8, cudaMemcpyDeviceToHost), "read counters");
+  LVQ_CUDA(s, cudaMemcpy(&live, root_of(s)->counters + kCtrLive, 8, cudaMemcpyDeviceToHost), "read counters");
   LVQ_CUDA(s, cudaMemcpy(&err, s->ds.err, 4, cudaMemcpyDeviceToHost), "read error word");
   *n_live_host = live;
   if (err) {

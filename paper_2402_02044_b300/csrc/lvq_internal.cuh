@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -30,6 +31,8 @@
 //   norm2   [capacity] f32    ||x^1||^2 of the first-level reconstruction
 //                             (used by the tensor-core L2 epilogue)
 //   live    [capacity/32] u32 bit s%32 of word s/32: slot s holds a vector
+//   reserved[capacity/32] u32 slot s is written by a deferred insert and not
+//                             yet published (neither free nor visible)
 //   means   [M][d] f32        centring means
 // ---------------------------------------------------------------------------
 
@@ -55,6 +58,7 @@ struct DeviceStore {
   uint8_t* mean_id;
   float* norm2;
   uint32_t* live;
+  uint32_t* reserved;
   float* means;
   int32_t* err;  // device error word (lvq_status of the first device error)
 };
@@ -65,7 +69,10 @@ struct lvq_store {
   lvq_config cfg;
   int device;
   lvq::DeviceStore ds;
-  int64_t rows_bound;  // no live slot at or beyond this index
+  // A view (lvq_store_view) shares the device arrays, counters and row bound
+  // of its base store and owns only its scratch memory, tuning and timing.
+  lvq_store* base = nullptr;
+  std::atomic<int64_t> rows_bound{0};  // (base only) no live slot at or beyond this index
   lvq_tuning tuning;
   // scratch memory (grown on demand, or pre-sized by lvq_reserve)
   void* ws = nullptr;

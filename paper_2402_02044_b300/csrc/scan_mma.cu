@@ -57,10 +57,11 @@ constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
 constexpr int kMaxQueryBytes = 196608;
-constexpr int kHistInts = 256 + 32;     // radix histogram, padded (see warp_kth)
+constexpr int kHistInts = 64;           // 6-bit-digit radix histogram of one warp
 
 struct MmaArgs {
   DeviceStore st;
+  int cm_table;       // <q, mu_m> of the query tile in shared memory: 0 no, 1 float16, 2 float32
   int64_t nq;
   QueryPrep p;
   int k1;
@@ -83,15 +84,15 @@ struct Smem {
   int total;
 };
 
-__host__ __device__ inline Smem smem_layout(int n, int qboxes, int stages) {
+__host__ __device__ inline Smem smem_layout(int n, int qboxes, int stages, int cm_bytes) {
   Smem s;
   s.q = 0;
   s.code = qboxes * n * 128;
   s.bars = s.code + stages * kStageBytes;
   s.misc = s.bars + 64 * 8;
-  // misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 + cnt[n] + qnorm[n] + cmax[n]
-  //       + hist[4][kHistInts]
-  s.total = s.misc + 32 + n * 8 + n * 16 + n * 4 * 3 + 4 * kHistInts * 4;
+  // misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 + qnorm[n] + cmabs[n]
+  //       + hist[4][kHistInts] + cm16[n][M] (when held)
+  s.total = s.misc + 32 + n * 8 + n * 16 + n * 4 * 2 + 4 * kHistInts * 4 + cm_bytes;
   return s;
 }
 
@@ -158,12 +159,13 @@ struct Ctx {
   uint32_t tbase;
   volatile int* abort_sh;
   uint64_t* thr;    // [N] exact key threshold (insert when key < thr)
-  float4* fq;       // [N] {sum(q), 1024 sum(q16), bound, 0}: a row may enter only if its
-                    //     filter value exceeds bound
-  int* cnt;
+  float4* fq;       // [N] {sum(q), 1024 sum(q16), bound, count}: a row may enter only if its
+                    //     filter value plus <q, mu_m> exceeds bound; count = keys buffered
   float* qnorm_s;
-  float* cmax_s;    // [N] max_m <q, mu_m>
-  int* hist;
+  float* cmabs_s;   // [N] max_m |<q, mu_m>|
+  int* hist;        // [4][kHistInts] radix histograms of the compacting warps
+  __half* cm16;     // [N][M] <q, mu_m> in float16, or null
+  float* cm32;      // [N][M] <q, mu_m> in float32, or null
   volatile int* ep_go;  // [2] epilogue leader's verdicts, read by the 4 epilogue warps after a named barrier
   int64_t u_begin, u_end;
   int cta, grid;
@@ -346,7 +348,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
   const DeviceStore& st = a.st;
   const bool ip = st.metric == LVQ_IP;
   uint64_t* mybuf = a.cand + (int64_t)c.cta * N * a.cap;
-  int* myhist = c.hist + (ew & 3) * kHistInts;
+  int* myhist = c.hist + (ew & 3) * kHistInts;  // used by warps 0-3
   uint32_t di = 0, pub = 0;
   // The eight epilogue warps meet at named barriers, so they must all take
   // the same path: only the first waits on mbarriers and reads the abort
@@ -360,15 +362,22 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
     if (et < N) {
       const bool real = q0 + et < a.nq;
       c.thr[et] = real ? kNoKey : 0ull;
-      c.cnt[et] = 0;
-      float cmax = __int_as_float(0xff800000);
+      float cmabs = 0.0f;
       if (real)
-        for (int m = 0; m < st.n_means; ++m) cmax = fmaxf(cmax, a.p.cm[(q0 + et) * st.n_means + m]);
-      c.cmax_s[et] = real ? cmax : 0.0f;
+        for (int m = 0; m < st.n_means; ++m) cmabs = fmaxf(cmabs, fabsf(a.p.cm[(q0 + et) * st.n_means + m]));
+      c.cmabs_s[et] = cmabs;
       c.qnorm_s[et] = real ? a.p.qnorm[q0 + et] : 0.0f;
       // absent queries take nothing (bound +inf), real ones everything (-inf)
       c.fq[et] = make_float4(real ? a.p.qsum[q0 + et] : 0.0f, real ? 1024.0f * a.p.q16sum[q0 + et] : 0.0f,
                              real ? __int_as_float(0xff800000) : __int_as_float(0x7f800000), 0.0f);
+    }
+    if (a.cm_table) {
+      for (int i = et; i < N * st.n_means; i += kEpiThreads) {
+        const int n = i / st.n_means;
+        const float v = q0 + n < a.nq ? a.p.cm[q0 * st.n_means + i] : 0.0f;
+        if (c.cm32) c.cm32[i] = v;
+        else c.cm16[i] = __float2half_rn(v);
+      }
     }
     if (et == 0) c.ep_go[pub & 1] = !*c.abort_sh;
     named_bar(1, kEpiThreads);
@@ -392,40 +401,58 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       if (t + 1 < t1) nxt = load_meta(a, (t + 1) * kRows + row_in, ip);
       const int64_t rw = t * kRows + row_in;
       const float* cm_row = a.p.cm + q0 * st.n_means + cur.m;
-      // Filter value: D <q16, c> + l sum(q) - ||x^||^2 / 2 (IP: no norm term).
-      // A row can beat the query's threshold only if it exceeds fq[n].z, a
-      // bound built with max_m <q, mu_m>; the rows that pass get their exact
-      // key (their <q, mu_m> loads issued together) and the exact test.
-#pragma unroll 1
-      for (int c0 = col0; c0 < col1; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld_x16<0>(lane_base + db * N + c0, v);
-        tmem_ld_wait();
-        uint32_t pass = 0;
-        float acc[16];
+      const __half* cm16_row = c.cm16 ? c.cm16 + cur.m : nullptr;
+      const float* cm32_row = c.cm32 ? c.cm32 + cur.m : nullptr;
+      // All of this warp's columns in one TMEM read.  The filter value
+      // D <q16, c> + l sum(q) - ||x^||^2 / 2 (IP: no norm term), plus
+      // <q, mu_m> (the shared-memory copy; 0 when not held), is compared with
+      // fq[n].z, the query's threshold minus a rounding margin (minus
+      // max_m |<q, mu_m>| without the copy): rows below it cannot beat the
+      // threshold.  The scores use the same <q, mu_m> as the filter.
+      constexpr int kPart = kHalf < 32 ? kHalf : 32;  // columns per TMEM read
+      uint64_t pass = 0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float4 f = c.fq[c0 + j];
-          acc[j] = __uint_as_float(v[j]) - f.y;
-          const float fv = __fmaf_rn(cur.lo, f.x, __fmaf_rn(cur.step, acc[j], cur.neg_h));
-          pass |= (fv > f.z ? 1u : 0u) << j;
+      for (int part = 0; part < kHalf / kPart; ++part) {
+        uint32_t v[kPart];
+        if constexpr (kPart == 16) {
+          tmem_ld_x16<0>(lane_base + db * N + col0, v);
+        } else {
+          tmem_ld_x32<0>(lane_base + db * N + col0 + part * 32, v);
         }
-        if (!cur.valid) pass = 0;
-        if (__any_sync(kFull, pass != 0)) {
-          float cmv[16];
+        tmem_ld_wait();
+        if (col0 < col1 && cur.valid) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            cmv[j] = ((pass >> j) & 1u) ? __ldg(cm_row + (c0 + j) * st.n_means) : 0.0f;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if ((pass >> j) & 1u) {
-              const int n = c0 + j;
-              float sc = __fmaf_rn(cur.step, acc[j], __fmaf_rn(cur.lo, c.fq[n].x, cmv[j]));
-              if (!ip) sc = c.qnorm_s[n] + cur.nrm - 2.0f * sc;
-              const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
-              if (key < c.thr[n]) mybuf[n * a.cap + atomicAdd(&c.cnt[n], 1)] = key;
-            }
+          for (int j = 0; j < kPart; ++j) {
+            const int n = col0 + part * kPart + j;
+            const float4 f = c.fq[n];
+            const float acc = __uint_as_float(v[j]) - f.y;
+            float fv = __fmaf_rn(cur.lo, f.x, __fmaf_rn(cur.step, acc, cur.neg_h));
+            if (cm32_row) fv += cm32_row[n * st.n_means];
+            else if (cm16_row) fv += __half2float(cm16_row[n * st.n_means]);
+            pass |= (uint64_t)(fv > f.z ? 1u : 0u) << (part * kPart + j);
           }
+        }
+      }
+      // Columns where some row of the warp passed, one at a time
+      // (warp-uniform), re-read from TMEM: the exact key and the exact test.
+      uint64_t any = pass;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(kFull, any, o);
+      while (any) {
+        const int j = __ffsll((long long)any) - 1;
+        any &= any - 1;
+        const int n = col0 + j;
+        const uint32_t raw = tmem_ld_x1(lane_base + db * N + n);
+        tmem_ld_wait();
+        if ((pass >> j) & 1ull) {
+          const float4 f = c.fq[n];
+          const float acc = __uint_as_float(raw) - f.y;
+          const float cmv = cm32_row ? cm32_row[n * st.n_means]
+                            : cm16_row ? __half2float(cm16_row[n * st.n_means]) : __ldg(cm_row + n * st.n_means);
+          float sc = __fmaf_rn(cur.step, acc, __fmaf_rn(cur.lo, f.x, cmv));
+          if (!ip) sc = c.qnorm_s[n] + cur.nrm - 2.0f * sc;
+          const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
+          if (key < c.thr[n]) mybuf[n * a.cap + atomicAdd(reinterpret_cast<int*>(&c.fq[n].w), 1)] = key;
         }
       }
       tc_fence_before();
@@ -434,22 +461,27 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       ++di;
       named_bar(1, kEpiThreads);
       if (ew < 4) {
+        // warps 0-3 compact the buffers that may not take another tile
         for (int n = ew; n < N; n += 4) {
-          if (c.cnt[n] > a.cap - kRows) {
+          const int cnt = __float_as_int(c.fq[n].w);
+          if (cnt > a.cap - kRows) {
             uint64_t tk;
-            const int kept = warp_select_small(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
+            const int kept = warp_select6(mybuf + n * a.cap, cnt, a.k1, myhist, &tk);
             if (lane == 0) {
-              c.cnt[n] = kept;
+              c.fq[n].w = __int_as_float(kept);
               c.thr[n] = tk;
               if (tk != kNoKey) {
-                // the new threshold score, turned into a bound on the filter value
+                // the new threshold score as a bound on the filter value (plus
+                // <q, mu_m>), less a margin for rounding
                 const float ts = key_score(tk, st.metric);
-                const float cm = c.cmax_s[n];
-                float b = ip ? ts - cm : 0.5f * (c.qnorm_s[n] - ts) - cm;
-                b -= 1e-5f * (fabsf(ts) + fabsf(cm) + c.qnorm_s[n]) + 1e-30f;
+                const float qn = c.qnorm_s[n];
+                float b = ip ? ts : 0.5f * (qn - ts);
+                b -= 1e-5f * (fabsf(ts) + qn + c.cmabs_s[n]) + 1e-30f;
+                if (!a.cm_table) b -= c.cmabs_s[n];
                 c.fq[n].z = b;
               }
             }
+            __syncwarp();
           }
         }
       }
@@ -464,7 +496,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
         for (int n = ew; n < N; n += 4) {
           if (q0 + n >= a.nq) continue;
           uint64_t tk;
-          const int kept = warp_select_small(mybuf + n * a.cap, c.cnt[n], a.k1, myhist, &tk);
+          const int kept = warp_select6(mybuf + n * a.cap, __float_as_int(c.fq[n].w), a.k1, myhist, &tk);
           uint64_t* dst = a.partial + ((q0 + n) * a.seg_max + seg) * a.k1;
           for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? mybuf[n * a.cap + i] : kNoKey;
         }
@@ -485,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const Smem L = smem_layout(N, a.qboxes, a.code_stages);
+  const Smem L = smem_layout(N, a.qboxes, a.code_stages, a.cm_table * N * a.st.n_means * 2);
   Ctx c;
   c.qs = smem + L.q;
   c.cst = smem + L.code;
@@ -494,10 +526,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.abort_sh = reinterpret_cast<volatile int*>(smem + L.misc + 16);
   c.thr = reinterpret_cast<uint64_t*>(smem + L.misc + 32);
   c.fq = reinterpret_cast<float4*>(c.thr + N);
-  c.cnt = reinterpret_cast<int*>(c.fq + N);
-  c.qnorm_s = reinterpret_cast<float*>(c.cnt + N);
-  c.cmax_s = c.qnorm_s + N;
-  c.hist = reinterpret_cast<int*>(c.cmax_s + N);
+  c.qnorm_s = reinterpret_cast<float*>(c.fq + N);
+  c.cmabs_s = c.qnorm_s + N;
+  c.hist = reinterpret_cast<int*>(c.cmabs_s + N);
+  c.cm16 = a.cm_table == 1 ? reinterpret_cast<__half*>(c.hist + 4 * kHistInts) : nullptr;
+  c.cm32 = a.cm_table == 2 ? reinterpret_cast<float*>(c.hist + 4 * kHistInts) : nullptr;
   c.ep_go = reinterpret_cast<volatile int*>(smem + L.misc + 20);  // two ints
   c.B = bars_at(bar_mem);
   c.grid = gridDim.x;
@@ -659,10 +692,17 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   if (e != cudaSuccess) return e;
   // as many code stages as shared memory allows (more bytes in flight for
   // narrow query tiles)
+  // The table of <q, mu_m> is held in float32 when it fits beside three
+  // code stages, else in float16 (scores then carry its rounding, at most
+  // 2^-11 |<q, mu_m>|), else not at all.
+  a.cm_table = 0;
+  for (int w = 2; w >= 1 && !a.cm_table; --w)
+    if ((size_t)smem_layout(n_tile, qboxes, 3, n_tile * st.n_means * 2 * w).total + 1024 <= 232448) a.cm_table = w;
+  const int cmb = n_tile * st.n_means * 2 * a.cm_table;
   a.code_stages = kMaxCodeStages;
-  while (a.code_stages > 2 && (size_t)smem_layout(n_tile, qboxes, a.code_stages).total + 1024 > 232448)
+  while (a.code_stages > 2 && (size_t)smem_layout(n_tile, qboxes, a.code_stages, cmb).total + 1024 > 232448)
     --a.code_stages;
-  const Smem L = smem_layout(n_tile, qboxes, a.code_stages);
+  const Smem L = smem_layout(n_tile, qboxes, a.code_stages, cmb);
   size_t smem = (size_t)L.total + 1024;
   if (smem < (size_t)kMinSmem) smem = kMinSmem;
   if (smem > 232448) return cudaErrorInvalidConfiguration;

@@ -94,6 +94,100 @@ __device__ __forceinline__ uint64_t warp_kth_regs(const uint64_t (&v)[E], int n,
   return prefix;
 }
 
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(kFull, v, o);
+    v = v < y ? v : y;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(kFull, v, o);
+    v = v > y ? v : y;
+  }
+  return v;
+}
+
+// The same select with 6-bit digits (64 bins: hist of 64 ints, lane l owning
+// bins 2l and 2l+1), for kernels short of shared memory.  The bits that all
+// keys share (the common prefix of the smallest and the largest) are skipped,
+// and lanes that fall in the same bin add to it once (warp-aggregated), so
+// keys with close scores do not serialise on one shared-memory counter.
+template <int E>
+__device__ __forceinline__ uint64_t warp_kth_regs6(const uint64_t (&v)[E], int n, int k, int* hist) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = kNoKey, hi = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (e * 32 + lane < n) {
+      lo = v[e] < lo ? v[e] : lo;
+      hi = v[e] > hi ? v[e] : hi;
+    }
+  lo = warp_min64(lo);
+  hi = warp_max64(hi);
+  if (lo == hi) return lo;
+  const int top = 63 - __clzll((long long)(lo ^ hi));  // highest bit where keys differ
+  uint64_t mask = top == 63 ? 0ull : ~((2ull << top) - 1ull);
+  uint64_t prefix = lo & mask;
+  for (int low = top - 5; low > -6; low -= 6) {
+    const int sh = low > 0 ? low : 0;
+    const int width = low >= 0 ? 6 : 6 + low;
+    const uint64_t dmask = (1ull << width) - 1ull;
+    hist[lane] = 0;
+    hist[lane + 32] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const bool in = e * 32 + lane < n && (v[e] & mask) == prefix;
+      const int b = in ? (int)((v[e] >> sh) & dmask) : 64 + lane;  // lanes out get distinct dummies
+      const unsigned same = __match_any_sync(kFull, b);
+      if (in && (__ffs(same) - 1) == lane) atomicAdd(&hist[b], __popc(same));
+    }
+    __syncwarp();
+    const int c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
+    const int s = c0 + c1;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - s;
+    const bool mine = excl < k && k <= incl;
+    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+    int bin = 0, before = 0, inbin = 0;
+    if (mine) {
+      if (k <= excl + c0) {
+        bin = 2 * lane;
+        before = excl;
+        inbin = c0;
+      } else {
+        bin = 2 * lane + 1;
+        before = excl + c0;
+        inbin = c1;
+      }
+    }
+    bin = __shfl_sync(kFull, bin, src);
+    before = __shfl_sync(kFull, before, src);
+    inbin = __shfl_sync(kFull, inbin, src);
+    k -= before;
+    prefix |= (uint64_t)bin << sh;
+    mask |= dmask << sh;
+    __syncwarp();
+    if (inbin == 1) {
+      uint64_t r = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (e * 32 + lane < n && (v[e] & mask) == prefix) r = v[e];
+      return warp_max64(r) | prefix;
+    }
+  }
+  return prefix;
+}
+
 // Keep the k smallest of the n distinct keys buf[0..n) at buf[0..kept),
 // unsorted; returns kept = min(n, k) and sets *thr to the k-th smallest key
 // when n >= k (else kNoKey).  One whole warp; n <= 32 * E.
@@ -207,6 +301,101 @@ __device__ __forceinline__ int warp_select_small(uint64_t* buf, int n, int k, in
   if (n <= 256) return warp_select_e<8>(buf, n, k, hist, thr);
   if (n <= 512) return warp_select_e<16>(buf, n, k, hist, thr);
   return warp_select_mem(buf, n, k, hist, thr);
+}
+
+// As warp_select_e with 6-bit digits (hist: 64 ints).
+template <int E>
+__device__ __forceinline__ int warp_select_e6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  const int lane = threadIdx.x & 31;
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = e * 32 + lane < n ? buf[e * 32 + lane] : kNoKey;
+  if (n <= k) {
+    *thr = (n == k && k > 0) ? warp_kth_regs6<E>(v, n, k, hist) : kNoKey;
+    __syncwarp();
+    return n;
+  }
+  const uint64_t t = warp_kth_regs6<E>(v, n, k, hist);
+  int pos = 0;
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const bool keep = e * 32 + lane < n && v[e] <= t;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = v[e];
+    pos += __popc(bal);
+  }
+  __syncwarp();
+  *thr = t;
+  return pos;
+}
+
+// 6-bit-digit select reading the keys from memory on every pass (for more
+// keys than a register-bound kernel can hold).
+__device__ __forceinline__ int warp_select_mem6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  const int lane = threadIdx.x & 31;
+  uint64_t prefix = 0, mask = 0;
+  int kk = k < n ? k : n;
+  for (int shift = 58; shift > -6 && kk > 0; shift -= 6) {
+    const int sh = shift > 0 ? shift : 0;
+    const uint64_t dmask = shift > 0 ? 63ull : (63ull >> (-shift));
+    hist[lane] = 0;
+    hist[lane + 32] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint64_t key = buf[i];
+      if ((key & mask) == prefix) atomicAdd(&hist[(int)((key >> sh) & dmask)], 1);
+    }
+    __syncwarp();
+    const int c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
+    const int sum = c0 + c1;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - sum;
+    const bool mine = excl < kk && kk <= incl;
+    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+    int bin = 0, before = 0;
+    if (mine) {
+      bin = kk <= excl + c0 ? 2 * lane : 2 * lane + 1;
+      before = kk <= excl + c0 ? excl : excl + c0;
+    }
+    bin = __shfl_sync(kFull, bin, src);
+    before = __shfl_sync(kFull, before, src);
+    kk -= before;
+    prefix |= (uint64_t)bin << sh;
+    mask |= dmask << sh;
+    __syncwarp();
+  }
+  if (n <= k) {
+    *thr = (n == k && k > 0) ? prefix : kNoKey;
+    return n;
+  }
+  const uint64_t t = prefix;
+  int pos = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint64_t key = i < n ? buf[i] : kNoKey;
+    const bool keep = i < n && key <= t;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    __syncwarp();
+    if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = key;
+    pos += __popc(bal);
+    __syncwarp();
+  }
+  *thr = t;
+  return pos;
+}
+
+// 6-bit-digit select (hist: 64 ints): up to 512 keys in registers, more
+// from memory.
+__device__ __forceinline__ int warp_select6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  if (n <= 256) return warp_select_e6<8>(buf, n, k, hist, thr);
+  if (n <= 512) return warp_select_e6<16>(buf, n, k, hist, thr);
+  return warp_select_mem6(buf, n, k, hist, thr);
 }
 
 // Runtime dispatch on the number of keys (held in registers); n <= 1024.

@@ -54,6 +54,9 @@ _SIGS = {
     "lvq_destroy": [_P],
     "lvq_encode": [_P, _P, _I64, _P, _P, _P, _P, _P, _P],
     "lvq_insert": [_P, _P, _I64, _P, _P],
+    "lvq_insert_deferred": [_P, _P, _I64, _P, _P],
+    "lvq_publish": [_P, _P, _I64, _P],
+    "lvq_store_view": [_P, ctypes.POINTER(_P)],
     "lvq_delete": [_P, _P, _I64, _P, _P],
     "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
@@ -148,6 +151,21 @@ def lvq_encode(store, x, codes1, codes2, lower, step, mean_id, stream=None):
 def lvq_insert(store, x, out_ids, stream=None):
     _check(load().lvq_insert(store, _ptr(x, torch.float32, "x"), x.shape[0], _ptr(out_ids, torch.int64, "out_ids"),
                              _stream(stream)), "lvq_insert")
+
+
+def lvq_insert_deferred(store, x, out_ids, stream=None):
+    _check(load().lvq_insert_deferred(store, _ptr(x, torch.float32, "x"), x.shape[0],
+                                      _ptr(out_ids, torch.int64, "out_ids"), _stream(stream)), "lvq_insert_deferred")
+
+
+def lvq_publish(store, ids, stream=None):
+    _check(load().lvq_publish(store, _ptr(ids, torch.int64, "ids"), ids.numel(), _stream(stream)), "lvq_publish")
+
+
+def lvq_store_view(store) -> int:
+    out = _P()
+    _check(load().lvq_store_view(store, ctypes.byref(out)), "lvq_store_view")
+    return out.value
 
 
 def lvq_delete(store, ids, out_n_deleted, stream=None):
@@ -270,6 +288,23 @@ class Store:
         ids = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
         lvq_insert(self.handle, x, ids, stream)
         return ids
+
+    def insert_deferred(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        ids = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
+        lvq_insert_deferred(self.handle, x, ids, stream)
+        return ids
+
+    def publish(self, ids: torch.Tensor, stream=None):
+        lvq_publish(self.handle, ids, stream)
+
+    def view(self) -> "Store":
+        """A handle sharing this store's data with its own scratch memory."""
+        v = Store.__new__(Store)
+        v.d, v.bits1, v.bits2, v.metric, v.capacity = self.d, self.bits1, self.bits2, self.metric, self.capacity
+        v.means = self.means
+        v.handle = lvq_store_view(self.handle)
+        v._base = self
+        return v
 
     def delete(self, ids: torch.Tensor, stream=None) -> torch.Tensor:
         out = torch.empty(1, dtype=torch.int64, device=ids.device)

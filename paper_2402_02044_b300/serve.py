@@ -1,0 +1,404 @@
+"""Continuous-batching serving loop over a device-resident LVQ store.
+
+Host-side scheduling only: every search, insert, delete and publication
+runs in liblvq's kernels through the C ABI.
+
+Model
+-----
+* Query requests (a [b, d] batch and a k) from many clients are concatenated
+  into one exhaustive search (one persistent scan launch over uneven request
+  sizes) and run on one of several *lanes*: a store view (own scratch
+  memory) with its own CUDA stream, so batches overlap on the device.  A
+  request's rows are re-split from the batch's results (the top-k of a query
+  is the first k of its top-k_max list).
+* Insert requests are encoded at once on an update stream with
+  ``lvq_insert_deferred``: their slots are written while searches run, but
+  stay invisible.  Deletes are queued.
+* Visibility changes at *epoch* boundaries: when updates are pending, the
+  scheduler stops starting new query batches, waits for the ones in flight,
+  publishes the pending inserts and applies the deletes, then resumes.  Every
+  query therefore sees exactly the store state of the epoch it ran in, and a
+  request's result is the same whether it ran alone or batched with others.
+* Admission: each request holds device bytes (its inputs and outputs) while
+  in flight; a request waits while the total would exceed the HBM budget,
+  and one that could never fit is rejected.
+* Optional CUDA graphs: per lane and per power-of-two batch size, the search
+  of a padded batch is captured once and replayed.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+import torch
+
+from .lvq import Store
+
+QUERY, INSERT, DELETE = "query", "insert", "delete"
+
+
+@dataclass
+class Request:
+    kind: str
+    data: np.ndarray
+    k: int = 0
+    future: Future = field(default_factory=Future)
+    t_submit: float = 0.0
+    nbytes: int = 0
+    epoch: int = -1
+
+
+def request_bytes(kind: str, n: int, d: int, k: int) -> int:
+    """Device bytes a request holds while in flight."""
+    if kind == QUERY:
+        return n * (4 * d + 12 * k)
+    if kind == INSERT:
+        return n * (4 * d + 8)
+    return n * 8 + 8
+
+
+class Admission:
+    """Byte budget for work in flight (pure host logic)."""
+
+    def __init__(self, budget: int):
+        self.budget = int(budget)
+        self.used = 0
+
+    def fits_ever(self, nbytes: int) -> bool:
+        return nbytes <= self.budget
+
+    def try_take(self, nbytes: int) -> bool:
+        if self.used + nbytes > self.budget:
+            return False
+        self.used += nbytes
+        return True
+
+    def give(self, nbytes: int):
+        self.used -= nbytes
+        assert self.used >= 0
+
+
+def form_batch(pending: "collections.deque[Request]", max_batch: int, admission: Admission):
+    """Take query requests from the head of the queue, in order, while the
+    batch stays within max_batch rows and the admission budget."""
+    batch, rows = [], 0
+    while pending:
+        r = pending[0]
+        n = r.data.shape[0]
+        if batch and rows + n > max_batch:
+            break
+        if not admission.try_take(r.nbytes):
+            break
+        pending.popleft()
+        batch.append(r)
+        rows += n
+        if rows >= max_batch:
+            break
+    return batch
+
+
+def bucket(n: int) -> int:
+    b = 1
+    while b < n:
+        b <<= 1
+    return b
+
+
+class LatencyStats:
+    def __init__(self):
+        self.lat = []
+        self.rows = 0
+        self.t0 = None
+        self.t1 = None
+
+    def add(self, t_submit: float, t_done: float, rows: int):
+        self.lat.append(t_done - t_submit)
+        self.rows += rows
+        self.t0 = t_submit if self.t0 is None else min(self.t0, t_submit)
+        self.t1 = t_done if self.t1 is None else max(self.t1, t_done)
+
+    def summary(self) -> dict:
+        if not self.lat:
+            return {"requests": 0}
+        a = np.asarray(self.lat) * 1e3
+        span = max(self.t1 - self.t0, 1e-9)
+        return {"requests": len(a), "p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+                "mean_ms": float(a.mean()), "qps": self.rows / span}
+
+
+class _Lane:
+    def __init__(self, store: Store, d: int, max_batch: int, kmax: int, k1: int):
+        self.view = store.view()
+        self.view.reserve(max_batch, max(k1, kmax))
+        self.stream = torch.cuda.Stream()
+        self.q_pin = torch.empty((max_batch, d), dtype=torch.float32).pin_memory()
+        self.q_dev = torch.zeros((max_batch, d), dtype=torch.float32, device="cuda")
+        self.ids_dev = torch.empty((max_batch, kmax), dtype=torch.int64, device="cuda")
+        self.sc_dev = torch.empty((max_batch, kmax), dtype=torch.float32, device="cuda")
+        self.ids_pin = torch.empty((max_batch, kmax), dtype=torch.int64).pin_memory()
+        self.sc_pin = torch.empty((max_batch, kmax), dtype=torch.float32).pin_memory()
+        self.graphs = {}
+        self.busy = None  # (event, batch, rows, kb)
+
+
+class Server:
+    def __init__(self, store: Store, lanes: int = 2, max_batch: int = 4096, k1: int = 100, kmax: int = 100,
+                 precision: str = "auto", hbm_budget: Optional[int] = None, use_graphs: bool = False,
+                 tuning: Optional[dict] = None):
+        self.store = store
+        self.d = store.d
+        self.k1 = k1 if store.bits2 else 0
+        self.kmax = kmax
+        self.max_batch = max_batch
+        self.precision = precision
+        self.use_graphs = use_graphs
+        self.tuning = tuning or {}
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            hbm_budget = free // 2
+        self.admission = Admission(hbm_budget)
+        self.lanes = [_Lane(store, self.d, max_batch, kmax, max(self.k1, kmax)) for _ in range(lanes)]
+        self.upd_stream = torch.cuda.Stream()
+        self.pending_q = collections.deque()
+        self.pending_upd = collections.deque()
+        self.staged = []          # (ids_dev, request) of deferred inserts awaiting publication
+        self.deletes = []         # delete requests awaiting the epoch boundary
+        self.inflight_upd = []    # (event, request, result tensor, kind)
+        self.epoch = 0
+        self.epoch_event = None
+        self.stats = LatencyStats()
+        self.rejected = 0
+        self._lock = threading.Lock()
+        self._wake = threading.Condition(self._lock)
+        self._stop = False
+        self._thread = threading.Thread(target=self._run, name="lvq-serve", daemon=True)
+        self._thread.start()
+
+    # ------------------------------------------------------------ client API
+    def submit_query(self, q: np.ndarray, k: int) -> Future:
+        q = np.ascontiguousarray(q, dtype=np.float32).reshape(-1, self.d)
+        if not 1 <= k <= self.kmax or q.shape[0] > self.max_batch:
+            raise ValueError("k or batch size out of range")
+        return self._submit(Request(QUERY, q, k, nbytes=request_bytes(QUERY, len(q), self.d, k)))
+
+    def submit_insert(self, x: np.ndarray) -> Future:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.d)
+        return self._submit(Request(INSERT, x, nbytes=request_bytes(INSERT, len(x), self.d, 0)))
+
+    def submit_delete(self, ids: np.ndarray) -> Future:
+        ids = np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
+        return self._submit(Request(DELETE, ids, nbytes=request_bytes(DELETE, len(ids), self.d, 0)))
+
+    def stats_summary(self) -> dict:
+        with self._lock:
+            s = self.stats.summary()
+            s.update(rejected=self.rejected, epochs=self.epoch, hbm_budget=self.admission.budget)
+            return s
+
+    def drain(self, timeout: float = 60.0):
+        """Wait until every submitted request has completed."""
+        t_end = time.time() + timeout
+        while time.time() < t_end:
+            with self._lock:
+                idle = (not self.pending_q and not self.pending_upd and not self.staged and not self.deletes
+                        and not self.inflight_upd and all(l.busy is None for l in self.lanes))
+            if idle:
+                return
+            time.sleep(0.001)
+        raise TimeoutError("serving loop did not drain")
+
+    def close(self):
+        with self._lock:
+            self._stop = True
+            self._wake.notify_all()
+        self._thread.join()
+        for l in self.lanes:
+            l.view.close()
+
+    def _submit(self, r: Request) -> Future:
+        r.t_submit = time.perf_counter()
+        with self._lock:
+            if not self.admission.fits_ever(r.nbytes):
+                self.rejected += 1
+                r.future.set_exception(MemoryError("request larger than the HBM budget"))
+                return r.future
+            (self.pending_q if r.kind == QUERY else self.pending_upd).append(r)
+            self._wake.notify_all()
+        return r.future
+
+    # ------------------------------------------------------------- scheduler
+    def _run(self):
+        torch.cuda.set_device(self.store_device())
+        while True:
+            with self._lock:
+                if self._stop:
+                    return
+                if not (self.pending_q or self.pending_upd or self.staged or self.deletes or self.inflight_upd
+                        or any(l.busy is not None for l in self.lanes)):
+                    self._wake.wait(timeout=0.01)
+                    continue
+            progressed = self._step()
+            if not progressed:
+                time.sleep(0.0002)
+
+    def store_device(self) -> int:
+        return torch.cuda.current_device()
+
+    def _step(self) -> bool:
+        progressed = self._complete()
+        progressed |= self._stage_updates()
+        updates_waiting = bool(self.staged or self.deletes)
+        if updates_waiting and all(l.busy is None for l in self.lanes) and not self.inflight_upd:
+            self._epoch_boundary()
+            progressed = True
+        elif not updates_waiting:
+            progressed |= self._launch_queries()
+        return progressed
+
+    def _complete(self) -> bool:
+        done_any = False
+        for lane in self.lanes:
+            if lane.busy is None or not lane.busy[0].query():
+                continue
+            _, batch, rows, kb = lane.busy
+            lane.busy = None
+            t = time.perf_counter()
+            ids = lane.ids_pin[:rows, :kb].numpy()
+            sc = lane.sc_pin[:rows, :kb].numpy()
+            off = 0
+            with self._lock:
+                for r in batch:
+                    n = r.data.shape[0]
+                    r.future.set_result((ids[off:off + n, :r.k].copy(), sc[off:off + n, :r.k].copy(), r.epoch))
+                    off += n
+                    self.admission.give(r.nbytes)
+                    self.stats.add(r.t_submit, t, n)
+            done_any = True
+        keep = []
+        for item in self.inflight_upd:
+            ev, r, res, kind = item
+            if not ev.query():
+                keep.append(item)
+                continue
+            with self._lock:
+                self.admission.give(r.nbytes)
+            if kind == DELETE:
+                r.future.set_result(int(res.item()))
+            done_any = True
+        self.inflight_upd = keep
+        return done_any
+
+    def _stage_updates(self) -> bool:
+        with self._lock:
+            if not self.pending_upd:
+                return False
+            reqs = []
+            while self.pending_upd and self.admission.try_take(self.pending_upd[0].nbytes):
+                reqs.append(self.pending_upd.popleft())
+        if not reqs:
+            return False
+        with torch.cuda.stream(self.upd_stream):
+            for r in reqs:
+                if r.kind == INSERT:
+                    x = torch.from_numpy(r.data).pin_memory().cuda(non_blocking=True)
+                    ids = self.store.insert_deferred(x, stream=self.upd_stream)
+                    self.staged.append((ids, x, r))
+                else:
+                    self.deletes.append(r)
+        return True
+
+    def _epoch_boundary(self):
+        """Publish staged inserts and apply queued deletes (no query in flight)."""
+        s = self.upd_stream
+        with torch.cuda.stream(s):
+            for ids, x, r in self.staged:
+                self.store.publish(ids, stream=s)
+                ids_host = ids.to("cpu", non_blocking=False)
+                r.future.set_result(ids_host.numpy())
+                with self._lock:
+                    self.admission.give(r.nbytes)
+            for r in self.deletes:
+                ids = torch.from_numpy(r.data).cuda(non_blocking=True)
+                out = self.store.delete(ids, stream=s)
+                ev = torch.cuda.Event()
+                ev.record(s)
+                self.inflight_upd.append((ev, r, out, DELETE))
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.staged, self.deletes = [], []
+        self.epoch_event = ev
+        self.epoch += 1
+
+    def _launch_queries(self) -> bool:
+        launched = False
+        for lane in self.lanes:
+            if lane.busy is not None:
+                continue
+            with self._lock:
+                batch = form_batch(self.pending_q, self.max_batch, self.admission)
+            if not batch:
+                break
+            rows = sum(r.data.shape[0] for r in batch)
+            kb = max(r.k for r in batch)
+            for r in batch:
+                r.epoch = self.epoch
+            self._run_batch(lane, batch, rows, kb)
+            launched = True
+        return launched
+
+    def _run_batch(self, lane: _Lane, batch, rows: int, kb: int):
+        off = 0
+        for r in batch:
+            n = r.data.shape[0]
+            lane.q_pin[off:off + n].copy_(torch.from_numpy(r.data))
+            off += n
+        s = lane.stream
+        with torch.cuda.stream(s):
+            if self.epoch_event is not None:
+                s.wait_event(self.epoch_event)
+            lane.q_dev[:rows].copy_(lane.q_pin[:rows], non_blocking=True)
+            kk = self.kmax if self.use_graphs else kb
+            nb = bucket(rows) if self.use_graphs else rows
+            if self.use_graphs:
+                g = lane.graphs.get(nb)
+                if g is None:
+                    g = self._capture(lane, nb)
+                g.replay()
+            else:
+                self._search(lane, nb, kk)
+            lane.ids_pin[:rows, :kk].copy_(lane.ids_dev[:rows, :kk], non_blocking=True)
+            lane.sc_pin[:rows, :kk].copy_(lane.sc_dev[:rows, :kk], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        lane.busy = (ev, batch, rows, kk)
+
+    def _search(self, lane: _Lane, nb: int, kk: int):
+        from .lvq import lvq_search_exhaustive
+        t = self.tuning.get(bucket(nb))
+        if t:
+            lane.view.set_tuning(**t)
+        ids = lane.ids_dev[:nb, :kk]
+        sc = lane.sc_dev[:nb, :kk]
+        if kk != lane.ids_dev.shape[1]:
+            ids = torch.empty((nb, kk), dtype=torch.int64, device="cuda")
+            sc = torch.empty((nb, kk), dtype=torch.float32, device="cuda")
+        lvq_search_exhaustive(lane.view.handle, lane.q_dev[:nb], self.k1, kk, self.precision, ids, sc,
+                              lane.stream)
+        if ids.data_ptr() != lane.ids_dev.data_ptr():
+            lane.ids_dev[:nb, :kk].copy_(ids)
+            lane.sc_dev[:nb, :kk].copy_(sc)
+
+    def _capture(self, lane: _Lane, nb: int):
+        # a warm-up call outside the capture sets kernel attributes and scratch
+        self._search(lane, nb, self.kmax)
+        lane.stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=lane.stream):
+            self._search(lane, nb, self.kmax)
+        lane.graphs[nb] = g
+        return g
