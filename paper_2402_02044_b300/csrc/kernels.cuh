@@ -1,6 +1,8 @@
 // Launchers of the LVQ kernels (called by the C ABI in lvq_api.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "lvq_internal.cuh"
 
 namespace lvq {
@@ -72,8 +74,19 @@ size_t mma_scan_cand_bytes(int grid, int n_tile, int k1);
 cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& p, int n_tile,
                             const ScanPlan& plan, cudaStream_t stream);
 bool mma_supported(const DeviceStore& st);
+cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm);
 int mma_tile_limit(const DeviceStore& st);   // largest query tile whose queries fit in shared memory
 int mma_seg_max(int grid, int64_t groups);   // segments per query tile in the partial lists
+
+// small-batch integer scan (scan_small.cu): queries quantised to 16-bit
+// integers (hi and lo bytes), codes as bytes, dp4a dot products on CUDA cores
+constexpr int kSmallMaxQ = 4;
+bool small_supported(const DeviceStore& st, int64_t nq, int k1);
+size_t small_scratch_bytes(const DeviceStore& st, int64_t nq);
+cudaError_t launch_scan_small(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                              void* scratch, const ScanPlan& plan, cudaStream_t stream);
+// persistent CTAs of the small-batch scan: one per SM, at most one per tile
+int small_grid(int64_t n_rows, int sm_count);
 
 // ---- selection and re-ranking ----------------------------------------------
 // Merge the per-split lists of each query into its k1 best, then either write

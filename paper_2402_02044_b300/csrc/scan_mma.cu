@@ -56,7 +56,6 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
-constexpr int kMaxQueryBytes = 196608;
 constexpr int kHistInts = 64;           // 6-bit-digit radix histogram of one warp
 
 struct MmaArgs {
@@ -121,32 +120,27 @@ __device__ __forceinline__ int cta_of_unit(int64_t u, int64_t units, int grid) {
   return (int)(((u + 1) * grid - 1) / units);
 }
 
-// float16 pairs of one 64-byte box of a row: 4-bit -> 64 pairs, 8-bit -> 32.
+// float16 pairs of half of a 64-byte box of a row (32 bytes, chunks 2h and
+// 2h+1): 4-bit -> 32 pairs (64 dims), 8-bit -> 16 pairs (32 dims, in r[0..15]).
 // 4-bit word (dims 8g..8g+7): the pair (2p, 2p+1) sits in bits 4p and 16+4p;
 // pairs 0 and 2 become (1024 + c, 1024 + c'), pairs 1 and 3 (1024 + 16c, ...).
 template <int BITS>
-__device__ __forceinline__ void unpack_box(const uint4 (&w)[4], uint32_t (&r)[64]) {
-  if (BITS == 4) {
+__device__ __forceinline__ void unpack_half(const uint4 (&w)[4], int h, uint32_t (&r)[32]) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+  for (int cc = 0; cc < 2; ++cc) {
+    const uint4 q = w[2 * h + cc];
+    const uint32_t ws[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4; ++i) {
+      if (BITS == 4) {
         const uint32_t hi = ws[i] >> 8;
-        r[c * 16 + i * 4 + 0] = (ws[i] & 0x000F000Fu) | 0x64006400u;
-        r[c * 16 + i * 4 + 1] = (ws[i] & 0x00F000F0u) | 0x64006400u;
-        r[c * 16 + i * 4 + 2] = (hi & 0x000F000Fu) | 0x64006400u;
-        r[c * 16 + i * 4 + 3] = (hi & 0x00F000F0u) | 0x64006400u;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        r[c * 8 + i * 2 + 0] = __byte_perm(ws[i], 0x64646464u, 0x5140);  // (1024 + b0, 1024 + b1)
-        r[c * 8 + i * 2 + 1] = __byte_perm(ws[i], 0x64646464u, 0x5342);  // (1024 + b2, 1024 + b3)
+        r[cc * 16 + i * 4 + 0] = (ws[i] & 0x000F000Fu) | 0x64006400u;
+        r[cc * 16 + i * 4 + 1] = (ws[i] & 0x00F000F0u) | 0x64006400u;
+        r[cc * 16 + i * 4 + 2] = (hi & 0x000F000Fu) | 0x64006400u;
+        r[cc * 16 + i * 4 + 3] = (hi & 0x00F000F0u) | 0x64006400u;
+      } else {
+        r[cc * 8 + i * 2 + 0] = __byte_perm(ws[i], 0x64646464u, 0x5140);  // (1024 + b0, 1024 + b1)
+        r[cc * 8 + i * 2 + 1] = __byte_perm(ws[i], 0x64646464u, 0x5342);  // (1024 + b2, 1024 + b3)
       }
     }
   }
@@ -294,14 +288,26 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         for (int q = 0; q < 4; ++q) w[q] = src[q ^ sw];
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.code_empty + s);
-        uint32_t r[64];
-        unpack_box<BITS>(w, r);
         const int as = ai % AS;
         LVQ_WAIT(c, c.B.a_empty + as, ((ai / AS) & 1) ^ 1);
         tc_fence_after();
         const uint32_t taddr = lane_base + 2 * N + as * kACols;
-        tmem_st_x32<0>(taddr, r);
-        if (BITS == 4) tmem_st_x32<32>(taddr + 32, r);
+        if (BITS == 4) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            unpack_half<BITS>(w, h, r);
+            tmem_st_x32<0>(taddr + 32 * h, r);
+          }
+        } else {
+          uint32_t r[32];
+          unpack_half<BITS>(w, 0, r);
+          uint32_t r2[32];
+          unpack_half<BITS>(w, 1, r2);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) r[16 + i] = r2[i];
+          tmem_st_x32<0>(taddr, r);
+        }
         tmem_st_wait();
         tc_fence_before();
         __syncwarp();
@@ -333,7 +339,9 @@ __device__ __forceinline__ RowMeta load_meta(const MmaArgs& a, int64_t rw, bool 
   return r;
 }
 
-template <int N, int BITS>
+// CM: how <q, mu_m> of the query tile is held in shared memory: 0 not at
+// all, 1 float16, 2 float32.
+template <int N, int BITS, int CM>
 __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, int warp, int lane) {
   const int quarter = warp & 3;
   const int ew = warp - kEpiWarp0;  // 0..7
@@ -371,11 +379,11 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       c.fq[et] = make_float4(real ? a.p.qsum[q0 + et] : 0.0f, real ? 1024.0f * a.p.q16sum[q0 + et] : 0.0f,
                              real ? __int_as_float(0xff800000) : __int_as_float(0x7f800000), 0.0f);
     }
-    if (a.cm_table) {
+    if (CM) {
       for (int i = et; i < N * st.n_means; i += kEpiThreads) {
         const int n = i / st.n_means;
         const float v = q0 + n < a.nq ? a.p.cm[q0 * st.n_means + i] : 0.0f;
-        if (c.cm32) c.cm32[i] = v;
+        if (CM == 2) c.cm32[i] = v;
         else c.cm16[i] = __float2half_rn(v);
       }
     }
@@ -401,14 +409,15 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       if (t + 1 < t1) nxt = load_meta(a, (t + 1) * kRows + row_in, ip);
       const int64_t rw = t * kRows + row_in;
       const float* cm_row = a.p.cm + q0 * st.n_means + cur.m;
-      const __half* cm16_row = c.cm16 ? c.cm16 + cur.m : nullptr;
-      const float* cm32_row = c.cm32 ? c.cm32 + cur.m : nullptr;
-      // All of this warp's columns in one TMEM read.  The filter value
+      const __half* cm16_row = c.cm16 + cur.m;
+      const float* cm32_row = c.cm32 + cur.m;
+      // This warp's columns, 32 at a time from TMEM.  The filter value
       // D <q16, c> + l sum(q) - ||x^||^2 / 2 (IP: no norm term), plus
       // <q, mu_m> (the shared-memory copy; 0 when not held), is compared with
       // fq[n].z, the query's threshold minus a rounding margin (minus
       // max_m |<q, mu_m>| without the copy): rows below it cannot beat the
-      // threshold.  The scores use the same <q, mu_m> as the filter.
+      // threshold.  The rows that pass get their exact key (with the same
+      // <q, mu_m>) and the exact test.
       constexpr int kPart = kHalf < 32 ? kHalf : 32;  // columns per TMEM read
       uint64_t pass = 0;
 #pragma unroll
@@ -420,19 +429,20 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
           tmem_ld_x32<0>(lane_base + db * N + col0 + part * 32, v);
         }
         tmem_ld_wait();
-        if (col0 < col1 && cur.valid) {
+        if (col0 < col1) {
 #pragma unroll
           for (int j = 0; j < kPart; ++j) {
             const int n = col0 + part * kPart + j;
             const float4 f = c.fq[n];
             const float acc = __uint_as_float(v[j]) - f.y;
             float fv = __fmaf_rn(cur.lo, f.x, __fmaf_rn(cur.step, acc, cur.neg_h));
-            if (cm32_row) fv += cm32_row[n * st.n_means];
-            else if (cm16_row) fv += __half2float(cm16_row[n * st.n_means]);
+            if (CM == 2) fv += cm32_row[n * st.n_means];
+            if (CM == 1) fv += __half2float(cm16_row[n * st.n_means]);
             pass |= (uint64_t)(fv > f.z ? 1u : 0u) << (part * kPart + j);
           }
         }
       }
+      if (!cur.valid) pass = 0;
       // Columns where some row of the warp passed, one at a time
       // (warp-uniform), re-read from TMEM: the exact key and the exact test.
       uint64_t any = pass;
@@ -447,8 +457,8 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
         if ((pass >> j) & 1ull) {
           const float4 f = c.fq[n];
           const float acc = __uint_as_float(raw) - f.y;
-          const float cmv = cm32_row ? cm32_row[n * st.n_means]
-                            : cm16_row ? __half2float(cm16_row[n * st.n_means]) : __ldg(cm_row + n * st.n_means);
+          const float cmv = CM == 2 ? cm32_row[n * st.n_means]
+                            : CM == 1 ? __half2float(cm16_row[n * st.n_means]) : __ldg(cm_row + n * st.n_means);
           float sc = __fmaf_rn(cur.step, acc, __fmaf_rn(cur.lo, f.x, cmv));
           if (!ip) sc = c.qnorm_s[n] + cur.nrm - 2.0f * sc;
           const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
@@ -466,7 +476,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
           const int cnt = __float_as_int(c.fq[n].w);
           if (cnt > a.cap - kRows) {
             uint64_t tk;
-            const int kept = warp_select6(mybuf + n * a.cap, cnt, a.k1, myhist, &tk);
+            const int kept = warp_prune(mybuf + n * a.cap, cnt, a.k1, a.k1 + (a.cap - kRows - a.k1) / 2, myhist, &tk);
             if (lane == 0) {
               c.fq[n].w = __int_as_float(kept);
               c.thr[n] = tk;
@@ -477,7 +487,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
                 const float qn = c.qnorm_s[n];
                 float b = ip ? ts : 0.5f * (qn - ts);
                 b -= 1e-5f * (fabsf(ts) + qn + c.cmabs_s[n]) + 1e-30f;
-                if (!a.cm_table) b -= c.cmabs_s[n];
+                if (CM == 0) b -= c.cmabs_s[n];
                 c.fq[n].z = b;
               }
             }
@@ -511,7 +521,7 @@ out:
 
 #undef LVQ_WAIT
 
-template <int N, int BITS>
+template <int N, int BITS, int CM>
 __global__ void __launch_bounds__(kThreads, 1)
     scan_mma_kernel(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap qmap, MmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -529,8 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.qnorm_s = reinterpret_cast<float*>(c.fq + N);
   c.cmabs_s = c.qnorm_s + N;
   c.hist = reinterpret_cast<int*>(c.cmabs_s + N);
-  c.cm16 = a.cm_table == 1 ? reinterpret_cast<__half*>(c.hist + 4 * kHistInts) : nullptr;
-  c.cm32 = a.cm_table == 2 ? reinterpret_cast<float*>(c.hist + 4 * kHistInts) : nullptr;
+  c.cm16 = reinterpret_cast<__half*>(c.hist + 4 * kHistInts);  // used when CM == 1
+  c.cm32 = reinterpret_cast<float*>(c.hist + 4 * kHistInts);   // used when CM == 2
   c.ep_go = reinterpret_cast<volatile int*>(smem + L.misc + 20);  // two ints
   c.B = bars_at(bar_mem);
   c.grid = gridDim.x;
@@ -575,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp < kEpiWarp0) {
     unpack_role<N, BITS>(a, c, warp, lane);
   } else {
-    epilogue_role<N, BITS>(a, c, warp, lane);
+    epilogue_role<N, BITS, CM>(a, c, warp, lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -609,27 +619,62 @@ int mma_cap(int k1) {
 }
 
 int max_n_tile(const DeviceStore& st) {
+  // the largest query tile whose queries fit in shared memory beside three
+  // code stages (and, below 128 queries, a float32 table of <q, mu_m>)
   const int qboxes = (int)ceil_div(st.row1, kBoxBytes) * (st.bits1 == 4 ? 2 : 1);
-  int n = 128;
-  while (n > 16 && qboxes * n * 128 > kMaxQueryBytes) n >>= 1;
-  return qboxes * n * 128 <= kMaxQueryBytes ? n : 0;
+  for (int n = 128; n >= 16; n >>= 1) {
+    const int cm = n < 128 ? n * st.n_means * 4 : 0;
+    if ((size_t)smem_layout(n, qboxes, 3, cm).total + 1024 <= 232448) return n;
+  }
+  return 0;
 }
 
-template <int N, int BITS>
-cudaError_t launch_nb(const CUtensorMap& cm, const CUtensorMap& qm, const MmaArgs& a, int grid, size_t smem,
-                      cudaStream_t stream) {
+template <int N, int BITS, int CM>
+cudaError_t launch_nbc(const CUtensorMap& cm, const CUtensorMap& qm, const MmaArgs& a, int grid, size_t smem,
+                       cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(scan_mma_kernel<N, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(scan_mma_kernel<N, BITS, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          232448);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  scan_mma_kernel<N, BITS><<<grid, kThreads, smem, stream>>>(cm, qm, a);
+  scan_mma_kernel<N, BITS, CM><<<grid, kThreads, smem, stream>>>(cm, qm, a);
   return cudaGetLastError();
 }
 
+// Query tiles of up to 64 queries always hold <q, mu_m> in float32 (it fits
+// for M <= 256); 128-query tiles hold it as space allows.
+template <int N, int BITS>
+cudaError_t launch_nb(const CUtensorMap& cm, const CUtensorMap& qm, const MmaArgs& a, int grid, size_t smem,
+                      cudaStream_t stream) {
+  if constexpr (N < 128) {
+    return launch_nbc<N, BITS, 2>(cm, qm, a, grid, smem, stream);
+  } else {
+    switch (a.cm_table) {
+      case 2: return launch_nbc<N, BITS, 2>(cm, qm, a, grid, smem, stream);
+      case 1: return launch_nbc<N, BITS, 1>(cm, qm, a, grid, smem, stream);
+      default: return launch_nbc<N, BITS, 0>(cm, qm, a, grid, smem, stream);
+    }
+  }
+}
+
 }  // namespace
+
+// Tensor map of the first-level codes: 128-row x 64-byte boxes, 64-byte
+// swizzle (shared by the tensor-core and the small-batch scans).
+cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)st.row1, (cuuint64_t)st.capacity};
+  cuuint64_t strides[1] = {(cuuint64_t)st.row1};
+  cuuint32_t box[2] = {(cuuint32_t)kBoxBytes, (cuuint32_t)kRows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(cm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, st.codes1, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 bool mma_supported(const DeviceStore& st) {
   return (st.bits1 == 4 || st.bits1 == 8) && max_n_tile(st) > 0 && encode_fn() != nullptr;
@@ -669,14 +714,8 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
 
   CUtensorMap cm, qm;
   {
-    cuuint64_t dims[2] = {(cuuint64_t)st.row1, (cuuint64_t)st.capacity};
-    cuuint64_t strides[1] = {(cuuint64_t)st.row1};
-    cuuint32_t box[2] = {(cuuint32_t)kBoxBytes, (cuuint32_t)kRows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&cm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, st.codes1, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const cudaError_t e = encode_code_map(st, &cm);
+    if (e != cudaSuccess) return e;
   }
   {
     cuuint64_t dims[2] = {(cuuint64_t)p.kq, (cuuint64_t)p.nq_pad};
@@ -698,6 +737,7 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   a.cm_table = 0;
   for (int w = 2; w >= 1 && !a.cm_table; --w)
     if ((size_t)smem_layout(n_tile, qboxes, 3, n_tile * st.n_means * 2 * w).total + 1024 <= 232448) a.cm_table = w;
+  if (n_tile < 128 && a.cm_table != 2) return cudaErrorInvalidConfiguration;  // narrow tiles always hold float32
   const int cmb = n_tile * st.n_means * 2 * a.cm_table;
   a.code_stages = kMaxCodeStages;
   while (a.code_stages > 2 && (size_t)smem_layout(n_tile, qboxes, a.code_stages, cmb).total + 1024 > 232448)

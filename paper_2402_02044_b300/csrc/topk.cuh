@@ -330,6 +330,96 @@ __device__ __forceinline__ int warp_select_e6(uint64_t* buf, int n, int k, int* 
   return pos;
 }
 
+// Ascending bitonic sort of one key per lane across the warp.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(kFull, v, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      v = (up == lower) ? (v < o ? v : o) : (v < o ? o : v);
+    }
+  }
+  return v;
+}
+
+// Approximate pruning of a candidate buffer of n <= 512 distinct keys: find
+// a threshold T among 32 sampled keys such that between k and keep_max keys
+// are below T, keep those (unsorted) and return their number; *thr = T, a
+// valid insertion threshold (at least k kept keys beat it).  Falls back to
+// the exact select when no sampled key qualifies.  hist: 64 ints.
+__device__ __forceinline__ int warp_prune(uint64_t* buf, int n, int k, int keep_max, int* hist, uint64_t* thr) {
+  const int lane = threadIdx.x & 31;
+  if (n <= keep_max) {
+    *thr = kNoKey;
+    return -1;  // nothing to do
+  }
+  uint64_t v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = e * 32 + lane < n ? buf[e * 32 + lane] : kNoKey;
+  // sample: lane l takes key l * n / 32 (spread over the buffer)
+  const int si = (lane * n) >> 5;
+  uint64_t smp = kNoKey;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const uint64_t x = __shfl_sync(kFull, v[e], si & 31);
+    if (e == (si >> 5)) smp = x;
+  }
+  smp = warp_sort32(smp);
+  // count of keys below sample j, by binary search on j
+  auto count_below = [&](uint64_t t) {
+    int c = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) c += __popc(__ballot_sync(kFull, e * 32 + lane < n && v[e] < t));
+    return c;
+  };
+  int lo_j = 0, hi_j = 31;
+  uint64_t t = kNoKey;
+  bool found = false;
+  for (int it = 0; it < 6 && lo_j <= hi_j; ++it) {
+    const int mid = (lo_j + hi_j) >> 1;
+    const uint64_t tm = __shfl_sync(kFull, smp, mid);
+    const int c = count_below(tm);
+    if (c < k) lo_j = mid + 1;
+    else if (c > keep_max) hi_j = mid - 1;
+    else {
+      t = tm;
+      found = true;
+      break;
+    }
+  }
+  if (!found) {
+    // exact k-th smallest; keep the k best
+    t = warp_kth_regs6<16>(v, n, k, hist);
+    int pos = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const bool keep = e * 32 + lane < n && v[e] <= t;
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = v[e];
+      pos += __popc(bal);
+    }
+    __syncwarp();
+    *thr = t;
+    return pos;
+  }
+  int pos = 0;
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const bool keep = e * 32 + lane < n && v[e] < t;
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (keep) buf[pos + __popc(bal & ((1u << lane) - 1u))] = v[e];
+    pos += __popc(bal);
+  }
+  __syncwarp();
+  *thr = t;
+  return pos;
+}
+
 // 6-bit-digit select reading the keys from memory on every pass (for more
 // keys than a register-bound kernel can hold).
 __device__ __forceinline__ int warp_select_mem6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
