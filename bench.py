@@ -54,8 +54,10 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="database size (default: the workload's)")
     ap.add_argument("--mix", default="full", choices=["full", "small"],
                     help="query mix: full = {1,4096} + 30 log-uniform in [1,4096]; small = 8 in [1,256]")
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "fp16", "int16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recall", action="store_true", help="skip the oracle recall sample")
+    ap.add_argument("--no-small", action="store_true", help="skip the small-batch roofline leg")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -118,6 +120,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def peaks_file() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -161,6 +171,37 @@ def cpu_baseline(mix, means, q_host, sample_rows=40_000, sample_queries=8, k1=10
             "sample": f"oracle brute-force search (first level over {sample_rows} rows of the workload, "
                       f"top-{k1}, two-level re-rank to top-{k}) for {sample_queries} queries; "
                       f"{dt:.2f} s; float64 decode + numpy/OpenBLAS"}
+
+
+def recall_sample(mix, means, q_host, precisions, n_rows=100_000, n_queries=8, k1=100, k=10):
+    """recall@10 of the GPU search against the oracle's exact k-NN over the
+    decoded vectors (and agreement with the oracle's own two-level search),
+    on a bounded slice of the workload: the first n_rows vectors, encoded by
+    both sides from the same means, and n_queries workload queries."""
+    import torch
+    import oracle as O
+    from paper_2402_02044_b300 import Store
+    x = mix.rows(0, n_rows)
+    q = q_host[:n_queries]
+    t0 = time.perf_counter()
+    enc = O.encode(x, means, 4, 8)
+    truth = O.ground_truth(enc, means, q, k, O.IP)[0]
+    two_level = O.search_exhaustive(enc, means, q, k1, k, O.IP)[0]
+    t_oracle = time.perf_counter() - t0
+    st = Store(x.shape[1], 4, 8, means, "ip", n_rows)
+    st.insert(torch.from_numpy(x).cuda())
+    qd = torch.from_numpy(q).cuda()
+    out = {"sample": f"first {n_rows} vectors of the workload, {n_queries} workload queries, k1={k1}, "
+                     f"oracle {t_oracle:.1f} s", "vs": "oracle exact top-10 over the decoded two-level vectors"}
+    for prec in precisions:
+        # the integer scan takes at most 4 queries per call
+        step = 4 if prec == "int16" else len(q)
+        ids = np.concatenate([st.search(qd[i:i + step], k, k1, prec)[0].cpu().numpy()
+                              for i in range(0, len(q), step)])
+        out[prec] = O.recall_at_k(ids, truth, k)
+        out[prec + "_vs_oracle_two_level"] = O.recall_at_k(ids, two_level, k)
+    st.close()
+    return out
 
 
 def run_reference(args):
@@ -332,14 +373,41 @@ def main():
         u2, t2 = aggregate(dist_per_step * args.steps, t_e2e, world)
         e2e = {"value": u2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # small batches: the integer scan against the HBM roofline
+    bytes_per_row = 384 + 4 + 4 + 1  # 4-bit codes, lower, step, mean id (IP reads no norm)
+    hbm_peak = peaks_file().get("hbm_gbs")
+    small = None
+    if not args.no_small:
+        small = []
+        for nqs in (1, 4):
+            qs = q_dev[:nqs].contiguous()
+            for _ in range(3):
+                st.search(qs, 10, 100, "auto")
+            torch.cuda.synchronize()
+            L.lvq_profile_enable(st.handle, True)
+            L.lvq_profile_read(st.handle)
+            reps = 20
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for _ in range(reps):
+                st.search(qs, 10, 100, "auto")
+            s1.record()
+            torch.cuda.synchronize()
+            p2 = L.lvq_profile_read(st.handle)
+            L.lvq_profile_enable(st.handle, False)
+            kind = max(("scan_small", "scan_mma", "scan_fp32"), key=lambda kk: p2[kk][1])
+            kms = p2[kind][0] / max(p2[kind][1], 1)
+            gbs = n_live * bytes_per_row / kms / 1e6
+            small.append({"nq": nqs, "kernel": kind, "kernel_ms": kms, "hbm_gbs": gbs, "peak_gbs": hbm_peak,
+                          "frac": gbs / hbm_peak if hbm_peak else None,
+                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else None,
+                          "search_ms": s0.elapsed_time(s1) / reps,
+                          "kernel_ms_per_search": {kk: v[0] / reps for kk, v in p2.items() if v[1]}})
+
     # roofline of the dominant kernel
     scan_kind = "scan_mma" if prof["scan_mma"][1] else "scan_fp32"
     scan_ms, scan_launches = prof[scan_kind]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = peaks_file()
     flops_per_launch = 2.0 * nq * n_live * d
     bytes_per_launch = n_live * (384 + 8 + 1)
     per_launch_s = scan_ms / 1e3 / max(scan_launches, 1)
@@ -371,12 +439,16 @@ def main():
                        "k1": 100, "k": 10, "gather_queries": nq_g, "gather_candidates": C,
                        "updates_per_step": B_upd, "l2_flush": "not needed: 3.9 GB of codes > 126 MB L2",
                        "precision": precision},
-            "qps": qps, "recall_at_10": None,
+            "qps": qps, "recall_at_10": None, "small_batch": small,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
             "setup_s": t_setup}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(mix, means, q_host)
+    if rank == 0 and not args.no_recall:
+        rec = recall_sample(mix, means, q_host, ["fp16", "fp32", "int16"])
+        line["recall_at_10"] = rec.get("fp16" if precision == "auto" else precision)
+        line["recall_sample"] = rec
     if rank == 0:
         print(json.dumps(line), flush=True)
     st.close()

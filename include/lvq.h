@@ -62,8 +62,12 @@ typedef enum { LVQ_L2 = 0, LVQ_IP = 1 } lvq_metric;
  *   LVQ_FP32      plain float32 on CUDA cores;
  *   LVQ_FP16_MMA  q rounded to float16, codes exact in float16, products
  *                 accumulated in float32 on the tcgen05 tensor cores;
- *   LVQ_AUTO      the library's choice for the batch size (tensor cores). */
-typedef enum { LVQ_FP32 = 0, LVQ_FP16_MMA = 1, LVQ_AUTO = 2 } lvq_precision;
+ *   LVQ_INT16     q rounded to 16-bit integers (scale max|q| / 32767 per
+ *                 query), exact integer products with the codes (dp4a) on
+ *                 CUDA cores; batches of at most 4 queries, else LVQ_EINVAL;
+ *   LVQ_AUTO      the library's choice for the batch size: LVQ_INT16 for 1
+ *                 to 4 queries, the tensor cores above that. */
+typedef enum { LVQ_FP32 = 0, LVQ_FP16_MMA = 1, LVQ_AUTO = 2, LVQ_INT16 = 3 } lvq_precision;
 
 typedef struct {
   int32_t d;        /* dimensionality, 1 .. 4096 */
@@ -207,7 +211,7 @@ lvq_status lvq_get_tuning(const lvq_store *store, lvq_tuning *tuning);
  * milliseconds and the launch count since the last read, then resets them.
  * ms and launches: host arrays of n_kinds entries (n_kinds <= LVQ_KERNEL_KINDS). */
 typedef enum {
-  LVQ_K_PREP = 0,       /* query preparation */
+  LVQ_K_PREP = 0,       /* query preparation (sums, norms, <q, mu_m>, rounding) */
   LVQ_K_SCAN_FP32 = 1,  /* float32 first-level scan */
   LVQ_K_SCAN_MMA = 2,   /* tcgen05 first-level scan */
   LVQ_K_MERGE = 3,      /* per-query merge of split lists (+ re-rank) */
@@ -215,7 +219,8 @@ typedef enum {
   LVQ_K_RERANK = 5,     /* lvq_rerank */
   LVQ_K_INSERT = 6,     /* slot allocation, encoding, publication */
   LVQ_K_DELETE = 7,     /* deletes */
-  LVQ_KERNEL_KINDS = 8
+  LVQ_K_SCAN_SMALL = 8,  /* small-batch integer first-level scan */
+  LVQ_KERNEL_KINDS = 9
 } lvq_kernel_kind;
 lvq_status lvq_profile_enable(lvq_store *store, int32_t on);
 lvq_status lvq_profile_read(lvq_store *store, double *ms, int64_t *launches, int32_t n_kinds);

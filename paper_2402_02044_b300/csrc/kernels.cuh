@@ -83,8 +83,10 @@ int mma_seg_max(int grid, int64_t groups);   // segments per query tile in the p
 constexpr int kSmallMaxQ = 4;
 bool small_supported(const DeviceStore& st, int64_t nq, int k1);
 size_t small_scratch_bytes(const DeviceStore& st, int64_t nq);
-cudaError_t launch_scan_small(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
-                              void* scratch, const ScanPlan& plan, cudaStream_t stream);
+// rounds the queries to 16-bit integers into scratch (small_scratch_bytes)
+cudaError_t launch_small_prep(const DeviceStore& st, const float* q, int64_t nq, void* scratch, cudaStream_t stream);
+cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep& p, const void* scratch,
+                              const ScanPlan& plan, cudaStream_t stream);
 // persistent CTAs of the small-batch scan: one per SM, at most one per tile
 int small_grid(int64_t n_rows, int sm_count);
 

@@ -93,19 +93,24 @@ int pick_mma_n(const lvq_store* s, int64_t nq) {
   return n > lim ? lim : n;
 }
 
+// First-level scan kernels.
+enum ScanPath { kPathFp32 = 0, kPathMma = 1, kPathSmall = 2 };
+
 // Layout of the scratch memory of a first-level scan.
 struct ScanScratch {
   QueryPrep prep;
   ScanPlan plan;
   int qb = 0, n_tile = 0;
-  bool mma = false;
+  int path = kPathFp32;
+  void* small = nullptr;  // rounded queries of the small-batch scan
 };
 
-size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, ScanScratch* out) {
+size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, ScanScratch* out) {
   const DeviceStore& st = s->ds;
+  const bool mma = path == kPathMma;
   Carver c(base);
   ScanScratch sc;
-  sc.mma = mma;
+  sc.path = path;
   sc.prep.qsum = c.take<float>(nq);
   sc.prep.qnorm = c.take<float>(nq);
   sc.prep.cm = c.take<float>((size_t)nq * st.n_means);
@@ -127,6 +132,11 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
     grid = s->sm_count;
     tiles_rows = 128;
     groups = sc.prep.nq_pad / sc.n_tile;
+  } else if (path == kPathSmall) {
+    sc.small = c.take<unsigned char>(small_scratch_bytes(st, nq));
+    grid = small_grid(n_rows, s->sm_count);
+    tiles_rows = 128;
+    groups = 1;
   } else {
     sc.qb = pick_qb(s, nq);
     grid = fp32_scan_grid(st, sc.qb, s->sm_count);
@@ -144,6 +154,10 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
     if (g < 1) g = 1;
     sc.plan.grid = g;
     splits = mma_seg_max(g, groups);
+  } else if (path == kPathSmall) {
+    // one contiguous range of tiles per CTA; each CTA writes its own list
+    sc.plan.grid = grid;
+    splits = grid;
   } else {
     splits = s->tuning.fp32_splits;
     if (splits <= 0) splits = (int)ceil_div((int64_t)grid * 2, groups);
@@ -155,8 +169,9 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, bool mma, void* base, S
   sc.plan.n_rows = n_rows;
   sc.plan.k1 = k1;
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
-  const size_t cand = mma ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
-                          : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);
+  const size_t cand = mma                  ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
+                     : path == kPathSmall ? 0
+                                          : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);
   sc.plan.cand = c.take<uint64_t>(cand / 8);
   if (out) *out = sc;
   return c.off;
@@ -193,29 +208,43 @@ lvq_status check_q(const lvq_store* s, const void* q, int64_t nq) {
 lvq_status first_level(lvq_store* s, const float* q, int64_t nq, int k1, int k, bool rerank, int precision,
                        int64_t* out_ids, float* out_scores, cudaStream_t stream) {
   const DeviceStore& st = s->ds;
-  bool mma;
-  if (precision == LVQ_FP32) mma = false;
-  else if (precision == LVQ_FP16_MMA || precision == LVQ_AUTO) mma = mma_supported(st);
-  else return fail(s, LVQ_EINVAL, "unknown precision");
-  if (precision == LVQ_FP16_MMA && !mma) return fail(s, LVQ_EINVAL, "tensor-core scan unavailable for this store");
+  int path;
+  if (precision == LVQ_FP32) {
+    path = kPathFp32;
+  } else if (precision == LVQ_FP16_MMA) {
+    if (!mma_supported(st)) return fail(s, LVQ_EINVAL, "tensor-core scan unavailable for this store");
+    path = kPathMma;
+  } else if (precision == LVQ_INT16) {
+    if (!small_supported(st, nq, k1) && nq > 0)
+      return fail(s, LVQ_EINVAL, "integer scan takes 1 to 4 queries of a 4- or 8-bit store");
+    path = kPathSmall;
+  } else if (precision == LVQ_AUTO) {
+    path = small_supported(st, nq, k1) ? kPathSmall : mma_supported(st) ? kPathMma : kPathFp32;
+  } else {
+    return fail(s, LVQ_EINVAL, "unknown precision");
+  }
   std::lock_guard<std::mutex> g(s->mu);
-  const size_t need = plan_scan(s, nq, k1, mma, nullptr, nullptr);
+  const size_t need = plan_scan(s, nq, k1, path, nullptr, nullptr);
   lvq_status rc = ensure_ws(s, need);
   if (rc != LVQ_OK) return rc;
   ScanScratch sc;
-  plan_scan(s, nq, k1, mma, s->ws, &sc);
+  plan_scan(s, nq, k1, path, s->ws, &sc);
   cudaError_t e;
   {
-    Prof p(s, stream, LVQ_K_PREP);
+    Prof p(s, stream, LVQ_K_PREP, path == kPathSmall ? 2 : 1);
     e = launch_prep_queries(st, q, nq, sc.prep, stream);
+    if (e == cudaSuccess && path == kPathSmall) e = launch_small_prep(st, q, nq, sc.small, stream);
   }
   if (e != cudaSuccess) return cuda_fail(s, e, "prep_queries");
+  static const int kind[3] = {LVQ_K_SCAN_FP32, LVQ_K_SCAN_MMA, LVQ_K_SCAN_SMALL};
+  static const char* name[3] = {"scan_fp32", "scan_mma", "scan_small"};
   {
-    Prof p(s, stream, mma ? LVQ_K_SCAN_MMA : LVQ_K_SCAN_FP32);
-    if (mma) e = launch_scan_mma(st, nq, sc.prep, sc.n_tile, sc.plan, stream);
+    Prof p(s, stream, kind[path]);
+    if (path == kPathMma) e = launch_scan_mma(st, nq, sc.prep, sc.n_tile, sc.plan, stream);
+    else if (path == kPathSmall) e = launch_scan_small(st, nq, sc.prep, sc.small, sc.plan, stream);
     else e = launch_scan_fp32(st, q, nq, sc.prep, sc.qb, sc.plan, stream);
   }
-  if (e != cudaSuccess) return cuda_fail(s, e, mma ? "scan_mma" : "scan_fp32");
+  if (e != cudaSuccess) return cuda_fail(s, e, name[path]);
   {
     Prof p(s, stream, LVQ_K_MERGE);
     e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, k1, k, rerank, out_ids,
@@ -528,9 +557,14 @@ lvq_status lvq_reserve(lvq_store* s, int64_t max_nq, int32_t max_k1, int32_t max
   if (!s || max_nq < 0 || max_k1 < 1 || max_k1 > kMaxK1 || max_cand < 0) return LVQ_EINVAL;
   (void)max_cand;
   std::lock_guard<std::mutex> g(s->mu);
-  size_t need = plan_scan(s, max_nq, max_k1, false, nullptr, nullptr);
+  size_t need = plan_scan(s, max_nq, max_k1, kPathFp32, nullptr, nullptr);
   if (mma_supported(s->ds)) {
-    const size_t m = plan_scan(s, max_nq, max_k1, true, nullptr, nullptr);
+    const size_t m = plan_scan(s, max_nq, max_k1, kPathMma, nullptr, nullptr);
+    if (m > need) need = m;
+  }
+  const int64_t small_nq = max_nq < kSmallMaxQ ? max_nq : kSmallMaxQ;
+  if (small_supported(s->ds, small_nq, max_k1)) {
+    const size_t m = plan_scan(s, small_nq, max_k1, kPathSmall, nullptr, nullptr);
     if (m > need) need = m;
   }
   return ensure_ws(s, need);

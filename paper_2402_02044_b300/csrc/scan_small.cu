@@ -1,0 +1,411 @@
+// First-level scan of small query batches (1 to 4 queries) on CUDA cores.
+//
+// A small batch reads every code byte once for a few dot products, so the
+// scan is bound by HBM, not by arithmetic, and is not reshaped into a
+// matrix product.  Each query is rounded to 16-bit integers,
+//   q ~ s * (256 hi + lo),  s = max|q| / 32767,  hi a signed, lo an unsigned byte,
+// and <q, c> ~ s * (256 sum hi_j c_j + sum lo_j c_j) is accumulated exactly
+// in 32-bit integers with dp4a (four byte products per instruction).  4-bit
+// codes become bytes with one mask each: (w & 0x0F0F0F0F) holds dims
+// (0, 4, 1, 5) of an 8-dim code word and ((w >> 4) & 0x0F0F0F0F) dims
+// (2, 6, 3, 7); the query bytes are stored in the same order.  Then
+//   IP: s = <q, mu_m> + l sum(q) + D <q, c>;   L2: ||q||^2 + ||x^||^2 - 2 s.
+//
+// One persistent CTA per SM scans a contiguous range of 128-row database
+// tiles.  Warp 0 streams each tile's 64-byte code boxes with TMA into one of
+// two 8-stage rings (even tiles, odd tiles); warps 1-4 and 5-8 are two
+// groups of 128 threads, one row per thread, that take the even and the odd
+// tiles.  Per query, scores below a running threshold go to a candidate
+// buffer in shared memory, which a warp cuts back to the k1 best when it
+// fills; at the end each CTA's k1 best go to partial[q][cta][.].
+#include <cudaTypedefs.h>
+
+#include "kernels.cuh"
+#include "score.cuh"
+#include "tcgen05.cuh"
+
+namespace lvq {
+
+namespace {
+
+using namespace sm100;
+
+constexpr int kRows = 128;
+constexpr int kBoxBytes = 64;
+constexpr int kStageBytes = kRows * kBoxBytes;
+constexpr int kRingStages = 8;  // per ring; two rings
+constexpr int kThreads = 32 * 9;
+constexpr int kConsumers = 256;
+constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr int kSmemLimit = 232448;
+
+struct SmallArgs {
+  DeviceStore st;
+  int64_t nq;
+  const uint32_t* qw;   // [nq][4][Wp]: A-hi, B-hi, A-lo, B-lo bytes per code word
+  const float* qscale;  // [nq]
+  QueryPrep p;
+  int Wp;               // code words per row, padded to whole boxes
+  int n_kbox;
+  int k1, cap;
+  int64_t n_rows, ntiles;
+  uint64_t* partial;    // [nq][gridDim.x][k1]
+};
+
+__device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t dp4a_uu(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Cuts a candidate buffer to its k best (kept out of line: the scan loop
+// and the select do not share registers).
+__device__ __noinline__ int select_k(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  return warp_select6(buf, n, k, hist, thr);
+}
+
+struct SmallSmem {
+  int ring, qw, fq, thr, cnt, cm, cand, hist, bars, total;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SmallSmem small_layout(int qb, int Wp, int M, int cap) {
+  SmallSmem s;
+  s.ring = 0;
+  s.qw = s.ring + 2 * kRingStages * kStageBytes;
+  s.fq = s.qw + qb * 4 * Wp * 4;
+  s.thr = s.fq + qb * 16;
+  s.cnt = s.thr + qb * 8;
+  s.cm = align_up(s.cnt + qb * 4 + 16, 16);
+  s.cand = align_up(s.cm + qb * M * 4, 16);
+  s.hist = s.cand + qb * cap * 8;
+  s.bars = align_up(s.hist + 4 * 64 * 4, 16);
+  s.total = s.bars + 2 * 2 * kRingStages * 8;
+  return s;
+}
+
+// QB: query slots (nq <= QB); BITS: first-level code width
+template <int QB, int BITS>
+__global__ void __launch_bounds__(kThreads, 1)
+    scan_small_kernel(const __grid_constant__ CUtensorMap cmap, SmallArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const DeviceStore& st = a.st;
+  const SmallSmem L = small_layout(QB, a.Wp, st.n_means, a.cap);
+  unsigned char* ring = smem + L.ring;
+  uint32_t* qw = reinterpret_cast<uint32_t*>(smem + L.qw);
+  float4* fq = reinterpret_cast<float4*>(smem + L.fq);  // {sum q, s, 0, ||q||^2}
+  uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
+  int* cnt = reinterpret_cast<int*>(smem + L.cnt);
+  volatile int* abort_sh = cnt + QB;
+  float* cmt = reinterpret_cast<float*>(smem + L.cm);
+  uint64_t* cand = reinterpret_cast<uint64_t*>(smem + L.cand);
+  int* hist = reinterpret_cast<int*>(smem + L.hist);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);  // [2][kRingStages]
+  uint64_t* empty = full + 2 * kRingStages;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t_begin = a.ntiles * blockIdx.x / gridDim.x;
+  const int64_t t_end = a.ntiles * (blockIdx.x + 1) / gridDim.x;
+  const bool ip = st.metric == LVQ_IP;
+  const int M = st.n_means;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * kRingStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 4);
+    }
+    *abort_sh = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < QB * 4 * a.Wp; i += kThreads) {
+    const int q = i / (4 * a.Wp);
+    qw[i] = q < a.nq ? a.qw[i] : 0u;
+  }
+  for (int i = threadIdx.x; i < QB * M; i += kThreads) {
+    const int q = i / M;
+    cmt[i] = q < a.nq ? a.p.cm[i] : 0.0f;
+  }
+  if (threadIdx.x < QB) {
+    const int q = threadIdx.x;
+    const bool real = q < a.nq;
+    thr[q] = kNoKey;
+    cnt[q] = 0;
+    fq[q] = make_float4(real ? a.p.qsum[q] : 0.0f, real ? a.qscale[q] : 0.0f, 0.0f, real ? a.p.qnorm[q] : 0.0f);
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- producer
+    if (lane == 0) {
+      prefetch_tmap(&cmap);
+      uint32_t fills[2] = {0u, 0u};
+      bool ok = true;
+      for (int64_t t = t_begin; t < t_end && ok && !*abort_sh; ++t) {
+        const int g = (int)((t - t_begin) & 1);
+        for (int kb = 0; kb < a.n_kbox; ++kb) {
+          const uint32_t ci = fills[g];
+          const int s = g * kRingStages + (int)(ci % kRingStages);
+          if (!mbar_wait(empty + s, ((ci / kRingStages) & 1) ^ 1, kWaitLimit)) {
+            *abort_sh = 1;
+            set_error(st.err, LVQ_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full + s, kStageBytes);
+          tma_load_2d(ring + s * kStageBytes, &cmap, full + s, kb * kBoxBytes, (int)(t * kRows));
+          fills[g] = ci + 1;
+        }
+      }
+      // let the copies still in flight land before the CTA can exit
+      for (int g = 0; g < 2; ++g)
+        for (uint32_t j = 1; j <= (uint32_t)kRingStages && j <= fills[g]; ++j) {
+          const uint32_t k = fills[g] - j;
+          mbar_wait(full + g * kRingStages + k % kRingStages, (k / kRingStages) & 1, kWaitLimit);
+        }
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    const int cw = warp - 1;   // 0..7
+    const int grp = cw >> 2;   // local tiles grp, grp + 2, ...
+    const int row = (cw & 3) * 32 + lane;
+    const int sw = (row >> 1) & 3;  // 64-byte swizzle of the box: chunk c sits at c ^ sw
+    uint32_t used = 0;         // boxes taken from this group's ring
+    bool go = true;
+    for (int64_t pair = t_begin; pair < t_end; pair += 2) {
+      const int64_t t = pair + grp;
+      if (t < t_end && go) {
+        int hi[QB];
+        uint32_t lo[QB];
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+          hi[q] = 0;
+          lo[q] = 0u;
+        }
+        const int64_t rw = t * kRows + row;
+        const bool valid = rw < a.n_rows && is_live(st.live, rw);
+        const int64_t ms = valid ? rw : 0;
+        const float lo_r = __ldg(st.lower + ms), step_r = __ldg(st.step + ms);
+        const int m_r = __ldg(st.mean_id + ms);
+        const float nrm = ip ? 0.0f : __ldg(st.norm2 + ms);
+        for (int kb = 0; kb < a.n_kbox; ++kb, ++used) {
+          const int s = grp * kRingStages + (int)(used % kRingStages);
+          if (!mbar_wait(full + s, (used / kRingStages) & 1, kWaitLimit)) {
+            if (lane == 0) {
+              *abort_sh = 1;
+              set_error(st.err, LVQ_ETIMEOUT);
+            }
+            go = false;
+            break;
+          }
+          const uint4* src = reinterpret_cast<const uint4*>(ring + s * kStageBytes + row * kBoxBytes);
+          uint4 w[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) w[c] = src[c ^ sw];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(empty + s);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+            const int word0 = kb * 16 + c * 4;
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+              const uint32_t* qq = qw + q * 4 * a.Wp + word0;
+              const uint4 ah = *reinterpret_cast<const uint4*>(qq);
+              const uint4 al = *reinterpret_cast<const uint4*>(qq + 2 * a.Wp);
+              const uint32_t ahs[4] = {ah.x, ah.y, ah.z, ah.w};
+              const uint32_t als[4] = {al.x, al.y, al.z, al.w};
+              if (BITS == 4) {
+                const uint4 bh = *reinterpret_cast<const uint4*>(qq + a.Wp);
+                const uint4 bl = *reinterpret_cast<const uint4*>(qq + 3 * a.Wp);
+                const uint32_t bhs[4] = {bh.x, bh.y, bh.z, bh.w};
+                const uint32_t bls[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const uint32_t A = ws[i] & 0x0F0F0F0Fu;
+                  const uint32_t B = (ws[i] >> 4) & 0x0F0F0F0Fu;
+                  hi[q] = dp4a_us(A, ahs[i], hi[q]);
+                  hi[q] = dp4a_us(B, bhs[i], hi[q]);
+                  lo[q] = dp4a_uu(A, als[i], lo[q]);
+                  lo[q] = dp4a_uu(B, bls[i], lo[q]);
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  hi[q] = dp4a_us(ws[i], ahs[i], hi[q]);
+                  lo[q] = dp4a_uu(ws[i], als[i], lo[q]);
+                }
+              }
+            }
+          }
+        }
+        if (go && valid) {
+#pragma unroll
+          for (int q = 0; q < QB; ++q) {
+            if (q < a.nq) {
+              const float4 f = fq[q];
+              const float dot = f.y * __fmaf_rn(256.0f, (float)hi[q], (float)lo[q]);
+              float sc = __fmaf_rn(step_r, dot, __fmaf_rn(lo_r, f.x, cmt[q * M + m_r]));
+              if (!ip) sc = f.w + nrm - 2.0f * sc;
+              const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
+              if (key < thr[q]) cand[q * a.cap + atomicAdd(&cnt[q], 1)] = key;
+            }
+          }
+        }
+      }
+      named_bar(1, kConsumers);
+      go = go && !*abort_sh;
+      // a full buffer (room for fewer than two more tiles) is cut to the k1 best
+      if (cw < QB && cw < a.nq && cnt[cw] > a.cap - 2 * kRows) {
+        uint64_t tk;
+        const int kept = select_k(cand + cw * a.cap, cnt[cw], a.k1, hist + cw * 64, &tk);
+        if (lane == 0) {
+          cnt[cw] = kept;
+          thr[cw] = tk;
+        }
+        __syncwarp();
+      }
+      named_bar(1, kConsumers);
+    }
+    if (cw < QB && cw < a.nq) {
+      uint64_t tk;
+      const int kept = select_k(cand + cw * a.cap, cnt[cw], a.k1, hist + cw * 64, &tk);
+      uint64_t* dst = a.partial + ((int64_t)cw * gridDim.x + blockIdx.x) * a.k1;
+      for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? cand[cw * a.cap + i] : kNoKey;
+    }
+  }
+}
+
+// Rounds each query to 16-bit integers and lays its bytes out in code-word
+// order (one warp per query).
+__global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
+                                                         int Wp, uint32_t* __restrict__ qw,
+                                                         float* __restrict__ qscale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nq) return;
+  const int d = st.d;
+  const float* qi = q + i * d;
+  float mx = 0.0f;
+  for (int j = lane; j < d; j += 32) mx = fmaxf(mx, fabsf(qi[j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float s = mx > 0.0f ? mx / 32767.0f : 1.0f;
+  const float inv = mx > 0.0f ? 32767.0f / mx : 0.0f;
+  if (lane == 0) qscale[i] = s;
+  uint32_t* out = qw + i * 4 * Wp;
+  auto qint = [&](int j) -> int {
+    return j < d ? max(-32767, min(32767, __float2int_rn(qi[j] * inv))) : 0;
+  };
+  for (int w = lane; w < Wp; w += 32) {
+    uint32_t ah = 0, bh = 0, al = 0, bl = 0;
+    if (st.bits1 == 4) {
+      const int oa[4] = {0, 4, 1, 5}, ob[4] = {2, 6, 3, 7};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int va = qint(8 * w + oa[b]), vb = qint(8 * w + ob[b]);
+        ah |= (uint32_t)((va >> 8) & 255) << (8 * b);
+        al |= (uint32_t)(va & 255) << (8 * b);
+        bh |= (uint32_t)((vb >> 8) & 255) << (8 * b);
+        bl |= (uint32_t)(vb & 255) << (8 * b);
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int va = qint(4 * w + b);
+        ah |= (uint32_t)((va >> 8) & 255) << (8 * b);
+        al |= (uint32_t)(va & 255) << (8 * b);
+      }
+    }
+    out[w] = ah;
+    out[Wp + w] = bh;
+    out[2 * Wp + w] = al;
+    out[3 * Wp + w] = bl;
+  }
+}
+
+template <int QB, int BITS>
+cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_t smem, cudaStream_t stream) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(scan_small_kernel<QB, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  scan_small_kernel<QB, BITS><<<grid, kThreads, smem, stream>>>(cm, a);
+  return cudaGetLastError();
+}
+
+int small_cap(int k1) { return pow2_at_least(k1 + 2 * kRows); }
+int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
+int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
+
+}  // namespace
+
+bool small_supported(const DeviceStore& st, int64_t nq, int k1) {
+  if (nq < 1 || nq > kSmallMaxQ || k1 < 1 || k1 > 1024) return false;
+  if (st.bits1 != 4 && st.bits1 != 8) return false;
+  if (!mma_supported(st)) return false;  // needs the driver's tensor-map encoder too
+  const SmallSmem L = small_layout(small_qb(nq), small_wp(st), st.n_means, small_cap(k1));
+  return L.total + 1024 <= kSmemLimit;
+}
+
+size_t small_scratch_bytes(const DeviceStore& st, int64_t nq) {
+  return (size_t)nq * 4 * small_wp(st) * 4 + (size_t)nq * 4 + 256;
+}
+
+int small_grid(int64_t n_rows, int sm_count) {
+  const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, kRows);
+  return (int)(ntiles < sm_count ? ntiles : sm_count);
+}
+
+cudaError_t launch_small_prep(const DeviceStore& st, const float* q, int64_t nq, void* scratch, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  const int Wp = small_wp(st);
+  uint32_t* qw = reinterpret_cast<uint32_t*>(scratch);
+  float* qscale = reinterpret_cast<float*>(qw + nq * 4 * Wp);
+  small_prep_kernel<<<(unsigned)ceil_div(nq, 8), 256, 0, stream>>>(st, q, nq, Wp, qw, qscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep& p, const void* scratch,
+                              const ScanPlan& plan, cudaStream_t stream) {
+  if (nq <= 0) return cudaSuccess;
+  if (nq > kSmallMaxQ || plan.splits != plan.grid) return cudaErrorInvalidValue;
+  SmallArgs a;
+  a.st = st;
+  a.nq = nq;
+  a.p = p;
+  a.Wp = small_wp(st);
+  const uint32_t* qw = reinterpret_cast<const uint32_t*>(scratch);
+  a.qw = qw;
+  a.qscale = reinterpret_cast<const float*>(qw + nq * 4 * a.Wp);
+  a.n_kbox = (int)ceil_div(st.row1, kBoxBytes);
+  a.k1 = plan.k1;
+  a.cap = small_cap(plan.k1);
+  a.n_rows = plan.n_rows;
+  a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, kRows);
+  a.partial = plan.partial;
+  CUtensorMap cm;
+  cudaError_t e = encode_code_map(st, &cm);
+  if (e != cudaSuccess) return e;
+  const int qb = small_qb(nq);
+  const size_t smem = (size_t)small_layout(qb, a.Wp, st.n_means, a.cap).total + 1024;
+  const int grid = plan.grid;
+  const bool b4 = st.bits1 == 4;
+  switch (qb) {
+    case 1: return b4 ? launch_qb<1, 4>(cm, a, grid, smem, stream) : launch_qb<1, 8>(cm, a, grid, smem, stream);
+    case 2: return b4 ? launch_qb<2, 4>(cm, a, grid, smem, stream) : launch_qb<2, 8>(cm, a, grid, smem, stream);
+    default: return b4 ? launch_qb<4, 4>(cm, a, grid, smem, stream) : launch_qb<4, 8>(cm, a, grid, smem, stream);
+  }
+}
+
+}  // namespace lvq

@@ -8,7 +8,7 @@ namespace lvq {
 
 namespace {
 
-// ---- query preparation (one warp per query) ---------------------------------
+// ---- query preparation (one warp per query; one per (query, mean) pair for <q, mu_m>)
 __global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
                                                    QueryPrep p) {
   const int lane = threadIdx.x & 31;
@@ -44,13 +44,18 @@ __global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* 
       p.qsum[i] = s;
       p.qnorm[i] = s2;
     }
-    for (int m = 0; m < st.n_means; ++m) {
-      const float* mu = st.means + (int64_t)m * d;
-      float c = 0.0f;
-      for (int j = lane; j < d; j += 32) c = __fmaf_rn(qi[j], __ldg(mu + j), c);
-      c = warp_sum(c);
-      if (lane == 0) p.cm[i * st.n_means + m] = c;
-    }
+  }
+  // <q_i, mu_m>: one warp per (query, mean) pair
+  const int64_t items = nq * st.n_means;
+  for (int64_t it = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); it < items; it += (int64_t)gridDim.x * warps) {
+    const int64_t i = it / st.n_means;
+    const int m = (int)(it - i * st.n_means);
+    const float* qi = q + i * d;
+    const float* mu = st.means + (int64_t)m * d;
+    float c = 0.0f;
+    for (int j = lane; j < d; j += 32) c = __fmaf_rn(qi[j], __ldg(mu + j), c);
+    c = warp_sum(c);
+    if (lane == 0) p.cm[it] = c;
   }
 }
 
@@ -78,6 +83,8 @@ __device__ void rerank_tail(const DeviceStore& st, const float* qsh, const uint6
 
 // ---- merge of per-split lists + optional re-rank (one block per query) --------
 constexpr int kMergeThreads = 128;
+constexpr int kMergePer = 8;
+constexpr int kMergeRound = kMergeThreads * kMergePer;
 
 __global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore st, const float* __restrict__ q,
                                                                       const uint64_t* __restrict__ partial,
@@ -85,7 +92,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore
                                                                       int64_t* out_ids, float* out_scores) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int qi = blockIdx.x;
-  const int cap = pow2_at_least(k1 + kMergeThreads);
+  const int cap = pow2_at_least(k1 + kMergeRound);
   uint64_t* buf = reinterpret_cast<uint64_t*>(smem);
   uint64_t* scratch = buf + cap;                   // pow2_at_least(k1) keys
   float* qsh = reinterpret_cast<float*>(scratch + pow2_at_least(k1));
@@ -101,28 +108,43 @@ __global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore
   __syncthreads();
   const uint64_t* src = partial + (int64_t)qi * splits * k1;
   const int total = splits * k1;
-  for (int base = 0; base < total; base += kMergeThreads) {
-    const int i = base + threadIdx.x;
-    if (i < total) {
-      const uint64_t key = src[i];
-      if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+  const int lane = threadIdx.x & 31;
+  // rounds of kMergeRound keys, kMergePer independent loads per thread
+  for (int base = 0; base < total; base += kMergeRound) {
+    uint64_t v[kMergePer];
+#pragma unroll
+    for (int r = 0; r < kMergePer; ++r) {
+      const int i = base + r * kMergeThreads + threadIdx.x;
+      v[r] = i < total ? __ldg(src + i) : kNoKey;
+    }
+    const uint64_t t = thr;
+#pragma unroll
+    for (int r = 0; r < kMergePer; ++r) {
+      const bool pass = v[r] < t;
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (m) {
+        int at = 0;
+        if (lane == 0) at = atomicAdd(&cnt, __popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (pass) buf[at + __popc(m & ((1u << lane) - 1u))] = v[r];
+      }
     }
     __syncthreads();
-    if (cnt > cap - kMergeThreads) {
+    if (cnt > cap - kMergeRound) {
       if (threadIdx.x < 32) {
-        uint64_t t;
-        const int kept = warp_select(buf, cnt, k1, hist, &t);
+        uint64_t tk;
+        const int kept = warp_select6(buf, cnt, k1, hist, &tk);
         if (threadIdx.x == 0) {
           cnt = kept;
-          thr = t;
+          thr = tk;
         }
       }
       __syncthreads();
     }
   }
   if (threadIdx.x < 32) {
-    uint64_t t;
-    const int kept = warp_select(buf, cnt, k1, hist, &t);
+    uint64_t tk;
+    const int kept = warp_select6(buf, cnt, k1, hist, &tk);
     if (threadIdx.x == 0) cnt = kept;
   }
   __syncthreads();
@@ -275,13 +297,14 @@ cudaError_t launch_prep_queries(const DeviceStore& st, const float* q, int64_t n
                                 cudaStream_t stream) {
   const int64_t rows = p.q16 ? (p.nq_pad > nq ? p.nq_pad : nq) : nq;
   if (rows <= 0) return cudaSuccess;
-  const int blocks = (int)(ceil_div(rows, 8) < 65536 ? ceil_div(rows, 8) : 65536);
+  const int64_t work = rows > nq * st.n_means ? rows : nq * st.n_means;
+  const int blocks = (int)(ceil_div(work, 8) < 65536 ? ceil_div(work, 8) : 65536);
   prep_kernel<<<blocks, 256, 0, stream>>>(st, q, nq, p);
   return cudaGetLastError();
 }
 
 static size_t merge_smem(int d, int k1) {
-  return (size_t)(pow2_at_least(k1 + kMergeThreads) + pow2_at_least(k1)) * 8 + (size_t)d * 4 +
+  return (size_t)(pow2_at_least(k1 + kMergeRound) + pow2_at_least(k1)) * 8 + (size_t)d * 4 +
          (size_t)(k1 + 2) * 4 + 16;
 }
 

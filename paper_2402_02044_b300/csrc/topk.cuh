@@ -420,51 +420,97 @@ __device__ __forceinline__ int warp_prune(uint64_t* buf, int n, int k, int keep_
   return pos;
 }
 
-// 6-bit-digit select reading the keys from memory on every pass (for more
-// keys than a register-bound kernel can hold).
+// warp_select6 for keys in shared memory (any n): 6-bit digits from the
+// highest bit where the keys differ, histogram increments aggregated over
+// lanes holding the same digit, stop once the k-th key's bin holds one key.
 __device__ __forceinline__ int warp_select_mem6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
   const int lane = threadIdx.x & 31;
-  uint64_t prefix = 0, mask = 0;
-  int kk = k < n ? k : n;
-  for (int shift = 58; shift > -6 && kk > 0; shift -= 6) {
-    const int sh = shift > 0 ? shift : 0;
-    const uint64_t dmask = shift > 0 ? 63ull : (63ull >> (-shift));
-    hist[lane] = 0;
-    hist[lane + 32] = 0;
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const uint64_t key = buf[i];
-      if ((key & mask) == prefix) atomicAdd(&hist[(int)((key >> sh) & dmask)], 1);
-    }
-    __syncwarp();
-    const int c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
-    const int sum = c0 + c1;
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int excl = incl - sum;
-    const bool mine = excl < kk && kk <= incl;
-    const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
-    int bin = 0, before = 0;
-    if (mine) {
-      bin = kk <= excl + c0 ? 2 * lane : 2 * lane + 1;
-      before = kk <= excl + c0 ? excl : excl + c0;
-    }
-    bin = __shfl_sync(kFull, bin, src);
-    before = __shfl_sync(kFull, before, src);
-    kk -= before;
-    prefix |= (uint64_t)bin << sh;
-    mask |= dmask << sh;
-    __syncwarp();
-  }
   if (n <= k) {
-    *thr = (n == k && k > 0) ? prefix : kNoKey;
+    uint64_t t = kNoKey;
+    if (n == k && k > 0) {
+      uint64_t m = 0;
+      for (int i = lane; i < n; i += 32) m = buf[i] > m ? buf[i] : m;
+      t = warp_max64(m);
+    }
+    *thr = t;
+    __syncwarp();
     return n;
   }
-  const uint64_t t = prefix;
+  uint64_t lo = kNoKey, hi = 0;
+  for (int i = lane; i < n; i += 32) {
+    const uint64_t key = buf[i];
+    lo = key < lo ? key : lo;
+    hi = key > hi ? key : hi;
+  }
+  lo = warp_min64(lo);
+  hi = warp_max64(hi);
+  uint64_t t = lo;
+  if (lo != hi) {
+    const int top = 63 - __clzll((long long)(lo ^ hi));
+    uint64_t mask = top == 63 ? 0ull : ~((2ull << top) - 1ull);
+    uint64_t prefix = lo & mask;
+    int kk = k;
+    bool done = false;
+    for (int low = top - 5; low > -6 && !done; low -= 6) {
+      const int sh = low > 0 ? low : 0;
+      const int width = low >= 0 ? 6 : 6 + low;
+      const uint64_t dmask = (1ull << width) - 1ull;
+      hist[lane] = 0;
+      hist[lane + 32] = 0;
+      __syncwarp();
+      const int rounds = (n + 31) >> 5;
+      for (int r = 0; r < rounds; ++r) {
+        const int i = r * 32 + lane;
+        const uint64_t key = i < n ? buf[i] : 0ull;
+        const bool in = i < n && (key & mask) == prefix;
+        const int b = in ? (int)((key >> sh) & dmask) : 64 + lane;
+        const unsigned same = __match_any_sync(kFull, b);
+        if (in && (__ffs(same) - 1) == lane) atomicAdd(&hist[b], __popc(same));
+      }
+      __syncwarp();
+      const int c0 = hist[2 * lane], c1 = hist[2 * lane + 1];
+      const int sum = c0 + c1;
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int excl = incl - sum;
+      const bool mine = excl < kk && kk <= incl;
+      const int src = __ffs(__ballot_sync(kFull, mine)) - 1;
+      int bin = 0, before = 0, inbin = 0;
+      if (mine) {
+        if (kk <= excl + c0) {
+          bin = 2 * lane;
+          before = excl;
+          inbin = c0;
+        } else {
+          bin = 2 * lane + 1;
+          before = excl + c0;
+          inbin = c1;
+        }
+      }
+      bin = __shfl_sync(kFull, bin, src);
+      before = __shfl_sync(kFull, before, src);
+      inbin = __shfl_sync(kFull, inbin, src);
+      kk -= before;
+      prefix |= (uint64_t)bin << sh;
+      mask |= dmask << sh;
+      __syncwarp();
+      if (inbin == 1) {
+        // the k-th key is the only one left under the prefix
+        uint64_t m = 0;
+        for (int i = lane; i < n; i += 32) {
+          const uint64_t key = buf[i];
+          if ((key & mask) == prefix) m = key;
+        }
+        prefix = warp_max64(m) | prefix;
+        done = true;
+      }
+    }
+    t = prefix;
+  }
   int pos = 0;
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;

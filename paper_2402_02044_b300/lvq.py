@@ -21,10 +21,10 @@ LIB_PATH = os.path.join(HERE, "liblvq.so")
 
 LVQ_OK, LVQ_EINVAL, LVQ_ENOMEM, LVQ_EFULL, LVQ_ENOTFOUND, LVQ_ECUDA, LVQ_ETIMEOUT, LVQ_EBUSY = range(8)
 LVQ_L2, LVQ_IP = 0, 1
-LVQ_FP32, LVQ_FP16_MMA, LVQ_AUTO = 0, 1, 2
+LVQ_FP32, LVQ_FP16_MMA, LVQ_AUTO, LVQ_INT16 = 0, 1, 2, 3
 
 METRICS = {"l2": LVQ_L2, "ip": LVQ_IP}
-PRECISIONS = {"fp32": LVQ_FP32, "fp16": LVQ_FP16_MMA, "auto": LVQ_AUTO}
+PRECISIONS = {"fp32": LVQ_FP32, "fp16": LVQ_FP16_MMA, "auto": LVQ_AUTO, "int16": LVQ_INT16}
 
 
 class lvq_config(ctypes.Structure):
@@ -72,7 +72,7 @@ _SIGS = {
     "lvq_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _I32],
 }
 
-KERNEL_KINDS = ["prep", "scan_fp32", "scan_mma", "merge", "gather", "rerank", "insert", "delete"]
+KERNEL_KINDS = ["prep", "scan_fp32", "scan_mma", "merge", "gather", "rerank", "insert", "delete", "scan_small"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
