@@ -18,7 +18,7 @@ enum { kCtrLive = 0, kCtrAbort = 1, kCtrDelCount = 2, kCtrWords = 4 };
 
 lvq_status fail(const lvq_store* s, lvq_status code, const char* msg) {
   if (s) {
-    std::lock_guard<std::mutex> g(s->mu);
+    std::lock_guard<std::mutex> g(s->msg_mu);
     s->last_msg = msg;
   }
   return code;
@@ -632,7 +632,7 @@ lvq_status lvq_last_error(const lvq_store* s, char* buf, size_t len) {
       msg = lvq_status_string(rc);
       cudaMemset(s->ds.err, 0, 4);
     } else {
-      std::lock_guard<std::mutex> g(s->mu);
+      std::lock_guard<std::mutex> g(s->msg_mu);
       msg = s->last_msg;
     }
   }

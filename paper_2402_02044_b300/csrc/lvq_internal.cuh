@@ -80,7 +80,8 @@ struct lvq_store {
   // small device-side counters used by insert / delete
   int64_t* counters = nullptr;
   int sm_count = 0;
-  mutable std::mutex mu;
+  mutable std::mutex mu;      // plan, scratch and tuning of calls
+  mutable std::mutex msg_mu;  // last_msg alone: errors are recorded while mu is held
   mutable std::string last_msg;
   // per-kernel timing (lvq_profile_enable)
   struct ProfRec {
