@@ -162,6 +162,26 @@ lvq_status lvq_search_exhaustive(const lvq_store *store, const float *q, int64_t
                                  int32_t k, int32_t precision, int64_t *out_ids,
                                  float *out_scores, lvq_stream_t stream);
 
+/* lvq_search_exhaustive at LVQ_INT16 for 1 to 4 queries, with no device
+ * memory allocated by the call.  The paper has no counterpart: it is a
+ * systems entry point for callers that must not allocate on the call path,
+ * because cudaMalloc/cudaFree there can synchronise the device and stall for
+ * milliseconds (a latency-bound serving thread) or fail once the process has
+ * given the rest of device memory to stores (lvq_search_exhaustive grows the
+ * store's scratch on demand).
+ * Scratch: a 4 MiB file-scope __device__ array of the library, one per
+ *   device, whose address is looked up (cudaGetSymbolAddress) on the first
+ *   call on each device; make that first call before any stream capture.
+ *   Nothing in it needs to start at zero.  Calls whose device work can
+ *   overlap (other streams, other stores on the same device) race on it:
+ *   issue them in order on one stream.
+ * Arguments and outputs as in lvq_search_exhaustive; nq outside 1 .. 4, a
+ * store or k1 the integer scan does not take, or a plan larger than the
+ * array return LVQ_EINVAL with a message (lvq_last_error). */
+lvq_status lvq_search_exhaustive_static(const lvq_store *store, const float *q, int64_t nq, int32_t k1,
+                                        int32_t k, int64_t *out_ids, float *out_scores,
+                                        lvq_stream_t stream);
+
 /* First stage alone: the k1 best live slots of each query by first-level
  * score, sorted, with their first-level scores (nq x k1 each). */
 lvq_status lvq_search_first_level(const lvq_store *store, const float *q, int64_t nq, int32_t k1,

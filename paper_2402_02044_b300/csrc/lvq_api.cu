@@ -2,6 +2,7 @@
 // sizing and the order of kernel launches of each call.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "kernels.cuh"
@@ -254,6 +255,18 @@ lvq_status first_level(lvq_store* s, const float* q, int64_t nq, int k1, int k, 
   return LVQ_OK;
 }
 
+// ---- scratch of lvq_search_exhaustive_static -----------------------------------
+// A file-scope device array, one per device (module global), so the call
+// allocates nothing: 4 MiB holds the largest small-batch plan (4 queries,
+// k1 = 512, one 512-key list per CTA on up to ~240 SMs, <q, mu_m> for 256
+// means, rounded queries of d = 4096).  No byte of it needs to start at
+// zero: every byte a call reads was written earlier in the same call.
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
 }  // namespace
 
 extern "C" {
@@ -460,6 +473,55 @@ lvq_status lvq_search_exhaustive(const lvq_store* cs, const float* q, int64_t nq
   if (nq == 0) return LVQ_OK;
   const bool two = s->ds.bits2 && k1 > 0;
   return first_level(s, q, nq, two ? k1 : k, k, two, precision, out_ids, out_scores, (cudaStream_t)stream);
+}
+
+lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t k,
+                                        int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  if (k < 1 || k > kMaxK1) return fail(s, LVQ_EINVAL, "k out of range");
+  if (k1 < 0 || k1 > kMaxK1 || (k1 > 0 && k1 < k)) return fail(s, LVQ_EINVAL, "k1 out of range");
+  if (nq < 1 || nq > kSmallMaxQ)
+    return fail(s, LVQ_EINVAL, "lvq_search_exhaustive_static takes 1 to 4 queries per call");
+  if (!out_ids || !out_scores) return fail(s, LVQ_EINVAL, "null output pointer");
+  const DeviceStore& st = s->ds;
+  const bool two = st.bits2 && k1 > 0;
+  const int kk1 = two ? k1 : k;
+  if (!small_supported(st, nq, kk1))
+    return fail(s, LVQ_EINVAL, "lvq_search_exhaustive_static: the integer scan does not take this store or k1");
+  // the scratch address on this device; the first call on a device looks it up
+  if (s->device < 0 || s->device >= kMaxDevices) return fail(s, LVQ_EINVAL, "device ordinal out of range");
+  void* base;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[s->device]) {
+      void* a = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+      if (e != cudaSuccess || !a) return cuda_fail(s, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+      g_static_addr[s->device] = a;
+    }
+    base = g_static_addr[s->device];
+  }
+  std::lock_guard<std::mutex> g(s->mu);
+  const size_t need = plan_scan(s, nq, kk1, kPathSmall, nullptr, nullptr);
+  if (need > kStaticScratchBytes) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "lvq_search_exhaustive_static: plan needs %zu bytes of scratch, the static array holds %zu",
+             need, kStaticScratchBytes);
+    return fail(s, LVQ_EINVAL, msg);
+  }
+  ScanScratch sc;
+  plan_scan(s, nq, kk1, kPathSmall, base, &sc);
+  const cudaStream_t str = (cudaStream_t)stream;
+  cudaError_t e = launch_prep_queries(st, q, nq, sc.prep, str);
+  if (e == cudaSuccess) e = launch_small_prep(st, q, nq, sc.small, str);
+  if (e != cudaSuccess) return cuda_fail(s, e, "prep_queries");
+  e = launch_scan_small(st, nq, sc.prep, sc.small, sc.plan, str);
+  if (e != cudaSuccess) return cuda_fail(s, e, "scan_small");
+  e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, kk1, k, two, out_ids, out_scores, str);
+  if (e != cudaSuccess) return cuda_fail(s, e, "merge_rerank");
+  return LVQ_OK;
 }
 
 lvq_status lvq_search_first_level(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t precision,

@@ -60,6 +60,7 @@ _SIGS = {
     "lvq_delete": [_P, _P, _I64, _P, _P],
     "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
+    "lvq_search_exhaustive_static": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
     "lvq_search_candidates": [_P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P],
     "lvq_rerank": [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P],
     "lvq_export": [_P, _P, _I64, _P, _P, _P, _P, _P, _P],
@@ -178,6 +179,13 @@ def lvq_search_exhaustive(store, q, k1, k, precision, out_ids, out_scores, strea
                                         PRECISIONS.get(precision, precision), _ptr(out_ids, torch.int64, "out_ids"),
                                         _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
            "lvq_search_exhaustive")
+
+
+def lvq_search_exhaustive_static(store, q, k1, k, out_ids, out_scores, stream=None):
+    _check(load().lvq_search_exhaustive_static(store, _ptr(q, torch.float32, "q"), q.shape[0], k1, k,
+                                               _ptr(out_ids, torch.int64, "out_ids"),
+                                               _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
+           "lvq_search_exhaustive_static")
 
 
 def lvq_search_first_level(store, q, k1, precision, out_ids, out_scores, stream=None):
