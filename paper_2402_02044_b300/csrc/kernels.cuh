@@ -74,7 +74,9 @@ size_t mma_scan_cand_bytes(int grid, int n_tile, int k1);
 cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& p, int n_tile,
                             const ScanPlan& plan, cudaStream_t stream);
 bool mma_supported(const DeviceStore& st);
-cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm);
+// TMA map of codes1 read in boxes of 128 rows x box_bytes (64: 64-byte
+// swizzle, 128: 128-byte swizzle)
+cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm, int box_bytes);
 int mma_tile_limit(const DeviceStore& st);   // largest query tile whose queries fit in shared memory
 int mma_seg_max(int grid, int64_t groups);   // segments per query tile in the partial lists
 

@@ -663,16 +663,17 @@ cudaError_t launch_nb(const CUtensorMap& cm, const CUtensorMap& qm, const MmaArg
 
 // Tensor map of the first-level codes: 128-row x 64-byte boxes, 64-byte
 // swizzle (shared by the tensor-core and the small-batch scans).
-cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm) {
+cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm, int box_bytes) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  if (box_bytes != 64 && box_bytes != 128) return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)st.row1, (cuuint64_t)st.capacity};
   cuuint64_t strides[1] = {(cuuint64_t)st.row1};
-  cuuint32_t box[2] = {(cuuint32_t)kBoxBytes, (cuuint32_t)kRows};
+  cuuint32_t box[2] = {(cuuint32_t)box_bytes, (cuuint32_t)kRows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(cm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, st.codes1, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, box_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -714,7 +715,7 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
 
   CUtensorMap cm, qm;
   {
-    const cudaError_t e = encode_code_map(st, &cm);
+    const cudaError_t e = encode_code_map(st, &cm, kBoxBytes);
     if (e != cudaSuccess) return e;
   }
   {

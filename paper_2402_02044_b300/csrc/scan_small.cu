@@ -12,12 +12,14 @@
 //   IP: s = <q, mu_m> + l sum(q) + D <q, c>;   L2: ||q||^2 + ||x^||^2 - 2 s.
 //
 // One persistent CTA per SM scans a contiguous range of 128-row database
-// tiles.  Warp 0 streams each tile's 64-byte code boxes with TMA into one of
-// two 8-stage rings (even tiles, odd tiles); warps 1-4 and 5-8 are two
-// groups of 128 threads, one row per thread, that take the even and the odd
-// tiles.  Per query, scores below a running threshold go to a candidate
-// buffer in shared memory, which a warp cuts back to the k1 best when it
-// fills; at the end each CTA's k1 best go to partial[q][cta][.].
+// tiles.  One thread of warp 0 streams each tile's 128-byte code boxes with
+// TMA into one of two rings (even tiles, odd tiles); warps 1-4 and
+// 5-8 are two groups of 128 threads, one row per thread, that take the even
+// and the odd tiles and run without waiting for each other.  Per query and
+// group, scores below a running threshold (the lower of the two groups')
+// go to a candidate buffer in shared memory, which a warp cuts back to the
+// k1 best when it fills; at the end each CTA's k1 best of the union go to
+// partial[q][cta][.].
 #include <cudaTypedefs.h>
 
 #include "kernels.cuh"
@@ -31,9 +33,10 @@ namespace {
 using namespace sm100;
 
 constexpr int kRows = 128;
-constexpr int kBoxBytes = 64;
+constexpr int kBoxBytes = 128;  // 128-byte swizzle: chunk c of row r sits at c ^ (r & 7)
+constexpr int kChunks = kBoxBytes / 16;
 constexpr int kStageBytes = kRows * kBoxBytes;
-constexpr int kRingStages = 8;  // per ring; two rings
+constexpr int kMaxRingStages = 8;  // per ring; two rings
 constexpr int kThreads = 32 * 9;
 constexpr int kConsumers = 256;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -47,6 +50,7 @@ struct SmallArgs {
   QueryPrep p;
   int Wp;               // code words per row, padded to whole boxes
   int n_kbox;
+  int stages;           // ring stages per ring
   int k1, cap;
   int64_t n_rows, ntiles;
   uint64_t* partial;    // [nq][gridDim.x][k1]
@@ -75,18 +79,19 @@ struct SmallSmem {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmallSmem small_layout(int qb, int Wp, int M, int cap) {
+// cand: [QB][2 groups][cap] keys; thr, cnt: [2][QB]; hist: 64 ints per consumer warp
+__host__ __device__ inline SmallSmem small_layout(int qb, int Wp, int M, int cap, int stages) {
   SmallSmem s;
   s.ring = 0;
-  s.qw = s.ring + 2 * kRingStages * kStageBytes;
+  s.qw = s.ring + 2 * stages * kStageBytes;
   s.fq = s.qw + qb * 4 * Wp * 4;
   s.thr = s.fq + qb * 16;
-  s.cnt = s.thr + qb * 8;
-  s.cm = align_up(s.cnt + qb * 4 + 16, 16);
+  s.cnt = s.thr + 2 * qb * 8;
+  s.cm = align_up(s.cnt + 2 * qb * 4 + 16, 16);
   s.cand = align_up(s.cm + qb * M * 4, 16);
-  s.hist = s.cand + qb * cap * 8;
-  s.bars = align_up(s.hist + 4 * 64 * 4, 16);
-  s.total = s.bars + 2 * 2 * kRingStages * 8;
+  s.hist = s.cand + qb * 2 * cap * 8;
+  s.bars = align_up(s.hist + 8 * 64 * 4, 16);
+  s.total = s.bars + 2 * 2 * stages * 8;
   return s;
 }
 
@@ -98,27 +103,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const DeviceStore& st = a.st;
-  const SmallSmem L = small_layout(QB, a.Wp, st.n_means, a.cap);
+  const int RS = a.stages;
+  const SmallSmem L = small_layout(QB, a.Wp, st.n_means, a.cap, RS);
   unsigned char* ring = smem + L.ring;
   uint32_t* qw = reinterpret_cast<uint32_t*>(smem + L.qw);
   float4* fq = reinterpret_cast<float4*>(smem + L.fq);  // {sum q, s, 0, ||q||^2}
   uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
   int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-  volatile int* abort_sh = cnt + QB;
+  volatile int* abort_sh = cnt + 2 * QB;
   float* cmt = reinterpret_cast<float*>(smem + L.cm);
   uint64_t* cand = reinterpret_cast<uint64_t*>(smem + L.cand);
   int* hist = reinterpret_cast<int*>(smem + L.hist);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);  // [2][kRingStages]
-  uint64_t* empty = full + 2 * kRingStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);  // [2][RS]
+  uint64_t* empty = full + 2 * RS;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t_begin = a.ntiles * blockIdx.x / gridDim.x;
   const int64_t t_end = a.ntiles * (blockIdx.x + 1) / gridDim.x;
   const bool ip = st.metric == LVQ_IP;
   const int M = st.n_means;
+  const int cap = a.cap;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2 * kRingStages; ++i) {
+    for (int i = 0; i < 2 * RS; ++i) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, 4);
     }
@@ -133,71 +140,98 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = i / M;
     cmt[i] = q < a.nq ? a.p.cm[i] : 0.0f;
   }
-  if (threadIdx.x < QB) {
-    const int q = threadIdx.x;
-    const bool real = q < a.nq;
-    thr[q] = kNoKey;
-    cnt[q] = 0;
-    fq[q] = make_float4(real ? a.p.qsum[q] : 0.0f, real ? a.qscale[q] : 0.0f, 0.0f, real ? a.p.qnorm[q] : 0.0f);
+  if (threadIdx.x < 2 * QB) {
+    const int q = threadIdx.x % QB;
+    thr[threadIdx.x] = kNoKey;
+    cnt[threadIdx.x] = 0;
+    if (threadIdx.x < QB) {
+      const bool real = q < a.nq;
+      fq[q] = make_float4(real ? a.p.qsum[q] : 0.0f, real ? a.qscale[q] : 0.0f, 0.0f, real ? a.p.qnorm[q] : 0.0f);
+    }
   }
   __syncthreads();
 
   if (warp == 0) {
     // ------------------------------------------------------------- producer
+    // Ring g carries the boxes of local tiles g, g + 2, ...; one thread keeps
+    // both rings full, refilling whichever has a free stage.
     if (lane == 0) {
       prefetch_tmap(&cmap);
+      int64_t next_t[2] = {t_begin, t_begin + 1};
+      int next_kb[2] = {0, 0};
       uint32_t fills[2] = {0u, 0u};
-      bool ok = true;
-      for (int64_t t = t_begin; t < t_end && ok && !*abort_sh; ++t) {
-        const int g = (int)((t - t_begin) & 1);
-        for (int kb = 0; kb < a.n_kbox; ++kb) {
+      uint32_t idle = 0;
+      while (!*abort_sh) {
+        bool left = false, moved = false;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          if (next_t[g] >= t_end) continue;
+          left = true;
           const uint32_t ci = fills[g];
-          const int s = g * kRingStages + (int)(ci % kRingStages);
-          if (!mbar_wait(empty + s, ((ci / kRingStages) & 1) ^ 1, kWaitLimit)) {
-            *abort_sh = 1;
-            set_error(st.err, LVQ_ETIMEOUT);
-            ok = false;
-            break;
-          }
+          const int s = g * RS + (int)(ci % RS);
+          if (!mbar_test_wait(empty + s, ((ci / RS) & 1) ^ 1)) continue;
           mbar_expect_tx(full + s, kStageBytes);
-          tma_load_2d(ring + s * kStageBytes, &cmap, full + s, kb * kBoxBytes, (int)(t * kRows));
+          tma_load_2d(ring + s * kStageBytes, &cmap, full + s, next_kb[g] * kBoxBytes, (int)(next_t[g] * kRows));
           fills[g] = ci + 1;
+          if (++next_kb[g] == a.n_kbox) {
+            next_kb[g] = 0;
+            next_t[g] += 2;
+          }
+          moved = true;
+        }
+        if (!left) break;
+        if (moved) {
+          idle = 0;
+        } else if (++idle > kWaitLimit) {
+          *abort_sh = 1;
+          set_error(st.err, LVQ_ETIMEOUT);
+          break;
+        } else {
+          __nanosleep(32);
         }
       }
       // let the copies still in flight land before the CTA can exit
       for (int g = 0; g < 2; ++g)
-        for (uint32_t j = 1; j <= (uint32_t)kRingStages && j <= fills[g]; ++j) {
+        for (uint32_t j = 1; j <= (uint32_t)RS && j <= fills[g]; ++j) {
           const uint32_t k = fills[g] - j;
-          mbar_wait(full + g * kRingStages + k % kRingStages, (k / kRingStages) & 1, kWaitLimit);
+          mbar_wait(full + g * RS + k % RS, (k / RS) & 1, kWaitLimit);
         }
     }
   } else {
     // ------------------------------------------------------------ consumers
-    const int cw = warp - 1;   // 0..7
-    const int grp = cw >> 2;   // local tiles grp, grp + 2, ...
-    const int row = (cw & 3) * 32 + lane;
-    const int sw = (row >> 1) & 3;  // 64-byte swizzle of the box: chunk c sits at c ^ sw
-    uint32_t used = 0;         // boxes taken from this group's ring
+    const int cw = warp - 1;        // 0..7
+    const int g = cw >> 2;          // group: local tiles g, g + 2, ...
+    const int wq = cw & 3;          // warp within the group
+    const int row = wq * 32 + lane;
+    const int sw = row & 7;  // 128-byte swizzle of the box: chunk c sits at c ^ sw
+    uint64_t* my_thr = thr + g * QB;
+    const uint64_t* other_thr = thr + (1 - g) * QB;
+    int* my_cnt = cnt + g * QB;
+    uint32_t used = 0;              // boxes taken from this group's ring
     bool go = true;
-    for (int64_t pair = t_begin; pair < t_end; pair += 2) {
-      const int64_t t = pair + grp;
-      if (t < t_end && go) {
-        int hi[QB];
-        uint32_t lo[QB];
+    for (int64_t t = t_begin + g; t < t_end; t += 2) {
+      if (go) {
+        // four independent accumulator chains per query: A/B halves (4-bit)
+        // or even/odd words (8-bit), high and low query bytes
+        int hi[QB][2];
+        uint32_t lo[QB][2];
 #pragma unroll
         for (int q = 0; q < QB; ++q) {
-          hi[q] = 0;
-          lo[q] = 0u;
+          hi[q][0] = hi[q][1] = 0;
+          lo[q][0] = lo[q][1] = 0u;
         }
+        // per-row constants and the live bit, all loaded now and first used
+        // after the boxes (no load waits on another)
         const int64_t rw = t * kRows + row;
-        const bool valid = rw < a.n_rows && is_live(st.live, rw);
-        const int64_t ms = valid ? rw : 0;
+        const bool in_range = rw < a.n_rows;
+        const int64_t ms = in_range ? rw : 0;
+        const uint32_t live_w = __ldg(st.live + (ms >> 5));
         const float lo_r = __ldg(st.lower + ms), step_r = __ldg(st.step + ms);
         const int m_r = __ldg(st.mean_id + ms);
         const float nrm = ip ? 0.0f : __ldg(st.norm2 + ms);
         for (int kb = 0; kb < a.n_kbox; ++kb, ++used) {
-          const int s = grp * kRingStages + (int)(used % kRingStages);
-          if (!mbar_wait(full + s, (used / kRingStages) & 1, kWaitLimit)) {
+          const int s = g * RS + (int)(used % RS);
+          if (!mbar_wait(full + s, (used / RS) & 1, kWaitLimit)) {
             if (lane == 0) {
               *abort_sh = 1;
               set_error(st.err, LVQ_ETIMEOUT);
@@ -206,15 +240,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           const uint4* src = reinterpret_cast<const uint4*>(ring + s * kStageBytes + row * kBoxBytes);
-          uint4 w[4];
+          uint4 w[kChunks];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) w[c] = src[c ^ sw];
+          for (int c = 0; c < kChunks; ++c) w[c] = src[c ^ sw];
           __syncwarp();
           if (lane == 0) mbar_arrive(empty + s);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < kChunks; ++c) {
             const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
-            const int word0 = kb * 16 + c * 4;
+            const int word0 = kb * (kBoxBytes / 4) + c * 4;
 #pragma unroll
             for (int q = 0; q < QB; ++q) {
               const uint32_t* qq = qw + q * 4 * a.Wp + word0;
@@ -231,54 +265,70 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < 4; ++i) {
                   const uint32_t A = ws[i] & 0x0F0F0F0Fu;
                   const uint32_t B = (ws[i] >> 4) & 0x0F0F0F0Fu;
-                  hi[q] = dp4a_us(A, ahs[i], hi[q]);
-                  hi[q] = dp4a_us(B, bhs[i], hi[q]);
-                  lo[q] = dp4a_uu(A, als[i], lo[q]);
-                  lo[q] = dp4a_uu(B, bls[i], lo[q]);
+                  hi[q][0] = dp4a_us(A, ahs[i], hi[q][0]);
+                  hi[q][1] = dp4a_us(B, bhs[i], hi[q][1]);
+                  lo[q][0] = dp4a_uu(A, als[i], lo[q][0]);
+                  lo[q][1] = dp4a_uu(B, bls[i], lo[q][1]);
                 }
               } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                  hi[q] = dp4a_us(ws[i], ahs[i], hi[q]);
-                  lo[q] = dp4a_uu(ws[i], als[i], lo[q]);
+                  hi[q][i & 1] = dp4a_us(ws[i], ahs[i], hi[q][i & 1]);
+                  lo[q][i & 1] = dp4a_uu(ws[i], als[i], lo[q][i & 1]);
                 }
               }
             }
           }
         }
+        const bool valid = in_range && ((live_w >> (ms & 31)) & 1u);
         if (go && valid) {
 #pragma unroll
           for (int q = 0; q < QB; ++q) {
             if (q < a.nq) {
               const float4 f = fq[q];
-              const float dot = f.y * __fmaf_rn(256.0f, (float)hi[q], (float)lo[q]);
+              const float h = (float)(hi[q][0] + hi[q][1]);
+              const float l = (float)lo[q][0] + (float)lo[q][1];
+              const float dot = f.y * __fmaf_rn(256.0f, h, l);
               float sc = __fmaf_rn(step_r, dot, __fmaf_rn(lo_r, f.x, cmt[q * M + m_r]));
               if (!ip) sc = f.w + nrm - 2.0f * sc;
               const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
-              if (key < thr[q]) cand[q * a.cap + atomicAdd(&cnt[q], 1)] = key;
+              // either group's threshold bounds the CTA's k1-th best
+              const uint64_t t1 = my_thr[q], t2 = other_thr[q];
+              if (key < (t1 < t2 ? t1 : t2)) cand[(q * 2 + g) * cap + atomicAdd(&my_cnt[q], 1)] = key;
             }
           }
         }
       }
-      named_bar(1, kConsumers);
+      named_bar(1 + g, 128);
       go = go && !*abort_sh;
-      // a full buffer (room for fewer than two more tiles) is cut to the k1 best
-      if (cw < QB && cw < a.nq && cnt[cw] > a.cap - 2 * kRows) {
+      // a buffer without room for another tile is cut to the k1 best
+      if (wq < QB && wq < a.nq && my_cnt[wq] > cap - kRows) {
         uint64_t tk;
-        const int kept = select_k(cand + cw * a.cap, cnt[cw], a.k1, hist + cw * 64, &tk);
+        const int kept = select_k(cand + (wq * 2 + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
         if (lane == 0) {
-          cnt[cw] = kept;
-          thr[cw] = tk;
+          my_cnt[wq] = kept;
+          my_thr[wq] = tk;
         }
         __syncwarp();
       }
-      named_bar(1, kConsumers);
+      named_bar(1 + g, 128);
     }
+    named_bar(3, kConsumers);
+    // the CTA's k1 best of each query: group 1's keys moved behind group 0's
     if (cw < QB && cw < a.nq) {
+      const int q = cw;
+      uint64_t* b0 = cand + (q * 2) * cap;
+      const int n0 = cnt[q], n1 = cnt[QB + q];
+      for (int base = 0; base < n1; base += 32) {
+        const uint64_t v = base + lane < n1 ? b0[cap + base + lane] : 0ull;
+        __syncwarp();
+        if (base + lane < n1) b0[n0 + base + lane] = v;
+        __syncwarp();
+      }
       uint64_t tk;
-      const int kept = select_k(cand + cw * a.cap, cnt[cw], a.k1, hist + cw * 64, &tk);
-      uint64_t* dst = a.partial + ((int64_t)cw * gridDim.x + blockIdx.x) * a.k1;
-      for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? cand[cw * a.cap + i] : kNoKey;
+      const int kept = select_k(b0, n0 + n1, a.k1, hist + cw * 64, &tk);
+      uint64_t* dst = a.partial + ((int64_t)q * gridDim.x + blockIdx.x) * a.k1;
+      for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? b0[i] : kNoKey;
     }
   }
 }
@@ -348,14 +398,21 @@ int small_cap(int k1) { return pow2_at_least(k1 + 2 * kRows); }
 int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
 int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
 
+// ring stages per ring: as many as shared memory holds, up to kMaxRingStages;
+// 0 when not even two fit
+int small_stages(const DeviceStore& st, int qb, int k1) {
+  for (int rs = kMaxRingStages; rs >= 2; --rs)
+    if (small_layout(qb, small_wp(st), st.n_means, small_cap(k1), rs).total + 1024 <= kSmemLimit) return rs;
+  return 0;
+}
+
 }  // namespace
 
 bool small_supported(const DeviceStore& st, int64_t nq, int k1) {
   if (nq < 1 || nq > kSmallMaxQ || k1 < 1 || k1 > 1024) return false;
   if (st.bits1 != 4 && st.bits1 != 8) return false;
   if (!mma_supported(st)) return false;  // needs the driver's tensor-map encoder too
-  const SmallSmem L = small_layout(small_qb(nq), small_wp(st), st.n_means, small_cap(k1));
-  return L.total + 1024 <= kSmemLimit;
+  return small_stages(st, small_qb(nq), k1) > 0;
 }
 
 size_t small_scratch_bytes(const DeviceStore& st, int64_t nq) {
@@ -394,11 +451,13 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
   a.n_rows = plan.n_rows;
   a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, kRows);
   a.partial = plan.partial;
-  CUtensorMap cm;
-  cudaError_t e = encode_code_map(st, &cm);
-  if (e != cudaSuccess) return e;
   const int qb = small_qb(nq);
-  const size_t smem = (size_t)small_layout(qb, a.Wp, st.n_means, a.cap).total + 1024;
+  a.stages = small_stages(st, qb, plan.k1);
+  if (a.stages == 0) return cudaErrorInvalidValue;
+  CUtensorMap cm;
+  cudaError_t e = encode_code_map(st, &cm, kBoxBytes);
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)small_layout(qb, a.Wp, st.n_means, a.cap, a.stages).total + 1024;
   const int grid = plan.grid;
   const bool b4 = st.bits1 == 4;
   switch (qb) {
