@@ -37,8 +37,8 @@ constexpr int kBoxBytes = 128;  // 128-byte swizzle: chunk c of row r sits at c 
 constexpr int kChunks = kBoxBytes / 16;
 constexpr int kStageBytes = kRows * kBoxBytes;
 constexpr int kMaxRingStages = 8;  // per ring; two rings
-constexpr int kThreads = 32 * 9;
-constexpr int kConsumers = 256;
+// groups of 4 consumer warps (one 128-row tile each at a time) + 1 producer warp
+__host__ __device__ constexpr int small_threads(int groups) { return 32 * (1 + 4 * groups); }
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kSmemLimit = 232448;
 
@@ -79,43 +79,44 @@ struct SmallSmem {
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// cand: [QB][2 groups][cap] keys; thr, cnt: [2][QB]; hist: 64 ints per consumer warp
-__host__ __device__ inline SmallSmem small_layout(int qb, int Wp, int M, int cap, int stages) {
+// cand: [QB][G groups][cap] keys; thr, cnt: [G][QB]; hist: 64 ints per consumer warp
+__host__ __device__ inline SmallSmem small_layout(int qb, int G, int Wp, int M, int cap, int stages) {
   SmallSmem s;
   s.ring = 0;
-  s.qw = s.ring + 2 * stages * kStageBytes;
+  s.qw = s.ring + G * stages * kStageBytes;
   s.fq = s.qw + qb * 4 * Wp * 4;
   s.thr = s.fq + qb * 16;
-  s.cnt = s.thr + 2 * qb * 8;
-  s.cm = align_up(s.cnt + 2 * qb * 4 + 16, 16);
+  s.cnt = s.thr + G * qb * 8;
+  s.cm = align_up(s.cnt + G * qb * 4 + 16, 16);
   s.cand = align_up(s.cm + qb * M * 4, 16);
-  s.hist = s.cand + qb * 2 * cap * 8;
-  s.bars = align_up(s.hist + 8 * 64 * 4, 16);
-  s.total = s.bars + 2 * 2 * stages * 8;
+  s.hist = s.cand + qb * G * cap * 8;
+  s.bars = align_up(s.hist + 4 * G * 64 * 4, 16);
+  s.total = s.bars + 2 * G * stages * 8;
   return s;
 }
 
-// QB: query slots (nq <= QB); BITS: first-level code width
-template <int QB, int BITS>
-__global__ void __launch_bounds__(kThreads, 1)
+// QB: query slots (nq <= QB); BITS: first-level code width; G: consumer groups
+template <int QB, int BITS, int G>
+__global__ void __launch_bounds__(small_threads(G), 1)
     scan_small_kernel(const __grid_constant__ CUtensorMap cmap, SmallArgs a) {
+  constexpr int kThreads = small_threads(G);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const DeviceStore& st = a.st;
   const int RS = a.stages;
-  const SmallSmem L = small_layout(QB, a.Wp, st.n_means, a.cap, RS);
+  const SmallSmem L = small_layout(QB, G, a.Wp, st.n_means, a.cap, RS);
   unsigned char* ring = smem + L.ring;
   uint32_t* qw = reinterpret_cast<uint32_t*>(smem + L.qw);
   float4* fq = reinterpret_cast<float4*>(smem + L.fq);  // {sum q, s, 0, ||q||^2}
   uint64_t* thr = reinterpret_cast<uint64_t*>(smem + L.thr);
   int* cnt = reinterpret_cast<int*>(smem + L.cnt);
-  volatile int* abort_sh = cnt + 2 * QB;
+  volatile int* abort_sh = cnt + G * QB;
   float* cmt = reinterpret_cast<float*>(smem + L.cm);
   uint64_t* cand = reinterpret_cast<uint64_t*>(smem + L.cand);
   int* hist = reinterpret_cast<int*>(smem + L.hist);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);  // [2][RS]
-  uint64_t* empty = full + 2 * RS;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);  // [G][RS]
+  uint64_t* empty = full + G * RS;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t_begin = a.ntiles * blockIdx.x / gridDim.x;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int cap = a.cap;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2 * RS; ++i) {
+    for (int i = 0; i < G * RS; ++i) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, 4);
     }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = i / M;
     cmt[i] = q < a.nq ? a.p.cm[i] : 0.0f;
   }
-  if (threadIdx.x < 2 * QB) {
+  if (threadIdx.x < G * QB) {
     const int q = threadIdx.x % QB;
     thr[threadIdx.x] = kNoKey;
     cnt[threadIdx.x] = 0;
@@ -157,14 +158,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     // both rings full, refilling whichever has a free stage.
     if (lane == 0) {
       prefetch_tmap(&cmap);
-      int64_t next_t[2] = {t_begin, t_begin + 1};
-      int next_kb[2] = {0, 0};
-      uint32_t fills[2] = {0u, 0u};
+      int64_t next_t[G];
+      int next_kb[G];
+      uint32_t fills[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        next_t[g] = t_begin + g;
+        next_kb[g] = 0;
+        fills[g] = 0u;
+      }
       uint32_t idle = 0;
       while (!*abort_sh) {
         bool left = false, moved = false;
 #pragma unroll
-        for (int g = 0; g < 2; ++g) {
+        for (int g = 0; g < G; ++g) {
           if (next_t[g] >= t_end) continue;
           left = true;
           const uint32_t ci = fills[g];
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           fills[g] = ci + 1;
           if (++next_kb[g] == a.n_kbox) {
             next_kb[g] = 0;
-            next_t[g] += 2;
+            next_t[g] += G;
           }
           moved = true;
         }
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // let the copies still in flight land before the CTA can exit
-      for (int g = 0; g < 2; ++g)
+      for (int g = 0; g < G; ++g)
         for (uint32_t j = 1; j <= (uint32_t)RS && j <= fills[g]; ++j) {
           const uint32_t k = fills[g] - j;
           mbar_wait(full + g * RS + k % RS, (k / RS) & 1, kWaitLimit);
@@ -200,16 +207,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ consumers
     const int cw = warp - 1;        // 0..7
-    const int g = cw >> 2;          // group: local tiles g, g + 2, ...
+    const int g = cw >> 2;          // group: local tiles g, g + G, ...
     const int wq = cw & 3;          // warp within the group
     const int row = wq * 32 + lane;
     const int sw = row & 7;  // 128-byte swizzle of the box: chunk c sits at c ^ sw
     uint64_t* my_thr = thr + g * QB;
-    const uint64_t* other_thr = thr + (1 - g) * QB;
     int* my_cnt = cnt + g * QB;
     uint32_t used = 0;              // boxes taken from this group's ring
     bool go = true;
-    for (int64_t t = t_begin + g; t < t_end; t += 2) {
+    for (int64_t t = t_begin + g; t < t_end; t += G) {
       if (go) {
         // four independent accumulator chains per query: A/B halves (4-bit)
         // or even/odd words (8-bit), high and low query bytes
@@ -292,9 +298,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               float sc = __fmaf_rn(step_r, dot, __fmaf_rn(lo_r, f.x, cmt[q * M + m_r]));
               if (!ip) sc = f.w + nrm - 2.0f * sc;
               const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
-              // either group's threshold bounds the CTA's k1-th best
-              const uint64_t t1 = my_thr[q], t2 = other_thr[q];
-              if (key < (t1 < t2 ? t1 : t2)) cand[(q * 2 + g) * cap + atomicAdd(&my_cnt[q], 1)] = key;
+              // every group's threshold bounds the CTA's k1-th best
+              uint64_t tq = thr[q];
+#pragma unroll
+              for (int h = 1; h < G; ++h) tq = thr[h * QB + q] < tq ? thr[h * QB + q] : tq;
+              if (key < tq) cand[(q * G + g) * cap + atomicAdd(&my_cnt[q], 1)] = key;
             }
           }
         }
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // a buffer without room for another tile is cut to the k1 best
       if (wq < QB && wq < a.nq && my_cnt[wq] > cap - kRows) {
         uint64_t tk;
-        const int kept = select_k(cand + (wq * 2 + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
+        const int kept = select_k(cand + (wq * G + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
         if (lane == 0) {
           my_cnt[wq] = kept;
           my_thr[wq] = tk;
@@ -313,20 +321,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       named_bar(1 + g, 128);
     }
-    named_bar(3, kConsumers);
-    // the CTA's k1 best of each query: group 1's keys moved behind group 0's
+    named_bar(1 + G, 4 * G * 32);
+    // the CTA's k1 best of each query: the other groups' keys moved behind
+    // group 0's (each move only writes below the next buffer's start)
     if (cw < QB && cw < a.nq) {
       const int q = cw;
-      uint64_t* b0 = cand + (q * 2) * cap;
-      const int n0 = cnt[q], n1 = cnt[QB + q];
-      for (int base = 0; base < n1; base += 32) {
-        const uint64_t v = base + lane < n1 ? b0[cap + base + lane] : 0ull;
-        __syncwarp();
-        if (base + lane < n1) b0[n0 + base + lane] = v;
-        __syncwarp();
+      uint64_t* b0 = cand + (q * G) * cap;
+      int n = cnt[q];
+      for (int h = 1; h < G; ++h) {
+        const int nh = cnt[h * QB + q];
+        for (int base = 0; base < nh; base += 32) {
+          const uint64_t v = base + lane < nh ? b0[h * cap + base + lane] : 0ull;
+          __syncwarp();
+          if (base + lane < nh) b0[n + base + lane] = v;
+          __syncwarp();
+        }
+        n += nh;
       }
       uint64_t tk;
-      const int kept = select_k(b0, n0 + n1, a.k1, hist + cw * 64, &tk);
+      const int kept = select_k(b0, n, a.k1, hist + cw * 64, &tk);
       uint64_t* dst = a.partial + ((int64_t)q * gridDim.x + blockIdx.x) * a.k1;
       for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? b0[i] : kNoKey;
     }
@@ -381,28 +394,32 @@ __global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const f
   }
 }
 
-template <int QB, int BITS>
+template <int QB, int BITS, int G>
 cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_t smem, cudaStream_t stream) {
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(scan_small_kernel<QB, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    const cudaError_t e = cudaFuncSetAttribute(scan_small_kernel<QB, BITS, G>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  scan_small_kernel<QB, BITS><<<grid, kThreads, smem, stream>>>(cm, a);
+  scan_small_kernel<QB, BITS, G><<<grid, small_threads(G), smem, stream>>>(cm, a);
   return cudaGetLastError();
 }
 
 int small_cap(int k1) { return pow2_at_least(k1 + 2 * kRows); }
 int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
 int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
+// consumer groups: three for one or two queries (more warps to hide the
+// latency of the loads), two for up to four (registers of four queries)
+int small_groups(int qb) { return qb <= 2 ? 3 : 2; }
 
 // ring stages per ring: as many as shared memory holds, up to kMaxRingStages;
 // 0 when not even two fit
 int small_stages(const DeviceStore& st, int qb, int k1) {
+  const int G = small_groups(qb);
   for (int rs = kMaxRingStages; rs >= 2; --rs)
-    if (small_layout(qb, small_wp(st), st.n_means, small_cap(k1), rs).total + 1024 <= kSmemLimit) return rs;
+    if (small_layout(qb, G, small_wp(st), st.n_means, small_cap(k1), rs).total + 1024 <= kSmemLimit) return rs;
   return 0;
 }
 
@@ -457,13 +474,13 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
   CUtensorMap cm;
   cudaError_t e = encode_code_map(st, &cm, kBoxBytes);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)small_layout(qb, a.Wp, st.n_means, a.cap, a.stages).total + 1024;
+  const size_t smem = (size_t)small_layout(qb, small_groups(qb), a.Wp, st.n_means, a.cap, a.stages).total + 1024;
   const int grid = plan.grid;
   const bool b4 = st.bits1 == 4;
   switch (qb) {
-    case 1: return b4 ? launch_qb<1, 4>(cm, a, grid, smem, stream) : launch_qb<1, 8>(cm, a, grid, smem, stream);
-    case 2: return b4 ? launch_qb<2, 4>(cm, a, grid, smem, stream) : launch_qb<2, 8>(cm, a, grid, smem, stream);
-    default: return b4 ? launch_qb<4, 4>(cm, a, grid, smem, stream) : launch_qb<4, 8>(cm, a, grid, smem, stream);
+    case 1: return b4 ? launch_qb<1, 4, 3>(cm, a, grid, smem, stream) : launch_qb<1, 8, 3>(cm, a, grid, smem, stream);
+    case 2: return b4 ? launch_qb<2, 4, 3>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3>(cm, a, grid, smem, stream);
+    default: return b4 ? launch_qb<4, 4, 2>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2>(cm, a, grid, smem, stream);
   }
 }
 
