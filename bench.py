@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true", help="skip the oracle recall sample")
     ap.add_argument("--no-small", action="store_true", help="skip the small-batch roofline leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -173,6 +174,56 @@ def cpu_baseline(mix, means, q_host, sample_rows=40_000, sample_queries=8, k1=10
                       f"{dt:.2f} s; float64 decode + numpy/OpenBLAS"}
 
 
+def serve_leg(st, mix, n, avoid, duration_s=6.0, rate=40.0, update_every_s=0.25, B_upd=10_000, seed=6006):
+    """p50/p99 latency of query requests served by the continuous-batching
+    loop under mixed load: Poisson arrivals (rate per second) of batches of
+    log-uniform size in [1, 4096] with k in {10, 100}, and every
+    update_every_s an insert of B_upd new vectors plus a delete of B_upd
+    live ones, all on the same store."""
+    from paper_2402_02044_b300.serve import Server
+    count = max(1, int(duration_s * rate))
+    t_arr = synth.poisson_arrivals(count, rate, seed)
+    sizes = synth.log_uniform_sizes(count, 1, 4096, seed + 1)
+    ks = np.where(synth.uniform_ints(count, 0, 1, seed + 2) == 0, 10, 100)
+    offs = synth.uniform_ints(count, 0, 4096, seed + 3, tag=4)
+    pool = mix.queries(8192)
+    n_upd = int(t_arr[-1] / update_every_s) + 1
+    cand = synth.choose(n, min(n, 3 * n_upd * B_upd), seed + 4)
+    cand = cand[~np.isin(cand, np.fromiter(avoid, dtype=np.int64, count=len(avoid)))][:n_upd * B_upd]
+    srv = Server(st, lanes=2, max_batch=4096, k1=100, kmax=100, precision="auto")
+    futs, upd = [], []
+    t0 = time.perf_counter()
+    next_upd, u = 0.0, 0
+    for i in range(count):
+        while True:
+            now = time.perf_counter() - t0
+            if u < n_upd and now >= next_upd and (u + 1) * B_upd <= len(cand):
+                upd.append(srv.submit_delete(cand[u * B_upd:(u + 1) * B_upd]))
+                upd.append(srv.submit_insert(mix.rows(u * B_upd, (u + 1) * B_upd, stream=13)))
+                u += 1
+                next_upd += update_every_s
+            if now >= t_arr[i]:
+                break
+            time.sleep(min(t_arr[i] - now, 0.0005))
+        futs.append(srv.submit_query(pool[offs[i]:offs[i] + sizes[i]], int(ks[i])))
+    for f in futs:
+        f.result(timeout=120)
+    failed = 0
+    for f in upd:
+        try:
+            f.result(timeout=120)
+        except Exception:
+            failed += 1
+    srv.drain()
+    s = srv.stats_summary()
+    srv.close()
+    return {"requests": s.get("requests"), "p50_ms": s.get("p50_ms"), "p99_ms": s.get("p99_ms"),
+            "mean_ms": s.get("mean_ms"), "qps": s.get("qps"), "epochs": s.get("epochs"),
+            "offered": f"{rate:g} query batches/s (Poisson, sizes log-uniform 1..4096, k in {{10, 100}}) for "
+                       f"{duration_s:g} s; every {update_every_s:g} s insert {B_upd} + delete {B_upd}",
+            "update_batches": 2 * u, "update_failures": failed, "lanes": 2, "precision": "auto"}
+
+
 def recall_sample(mix, means, q_host, precisions, n_rows=100_000, n_queries=8, k1=100, k=10):
     """recall@10 of the GPU search against the oracle's exact k-NN over the
     decoded vectors (and agreement with the oracle's own two-level search),
@@ -261,7 +312,7 @@ def main():
     means = synth.kmeans_means(sample, w["n_means"], seed=3003, iters=25)
     B_upd = 10_000
     steps_total = args.warmup + 2 * args.steps
-    st = Store(d, 4, 8, means, "ip", n)
+    st = Store(d, 4, 8, means, "ip", n + 100_000)  # spare slots for the serving leg's inserts
     chunk = 1 << 20
     for s in range(0, n, chunk):
         xs = torch.from_numpy(mix.rows(s, min(n, s + chunk))).cuda()
@@ -404,6 +455,10 @@ def main():
                           "search_ms": s0.elapsed_time(s1) / reps,
                           "kernel_ms_per_search": {kk: v[0] / reps for kk, v in p2.items() if v[1]}})
 
+    serve = None
+    if not args.no_serve:
+        serve = serve_leg(st, mix, n, used)
+
     # roofline of the dominant kernel
     scan_kind = "scan_mma" if prof["scan_mma"][1] else "scan_fp32"
     scan_ms, scan_launches = prof[scan_kind]
@@ -439,7 +494,7 @@ def main():
                        "k1": 100, "k": 10, "gather_queries": nq_g, "gather_candidates": C,
                        "updates_per_step": B_upd, "l2_flush": "not needed: 3.9 GB of codes > 126 MB L2",
                        "precision": precision},
-            "qps": qps, "recall_at_10": None, "small_batch": small,
+            "qps": qps, "recall_at_10": None, "small_batch": small, "serve": serve,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
             "setup_s": t_setup}

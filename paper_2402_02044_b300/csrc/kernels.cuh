@@ -62,7 +62,9 @@ struct ScanPlan {
   uint64_t* partial;    // [nq][splits][k1]
   uint64_t* cand;       // per-CTA candidate buffers
   int grid;             // persistent CTAs
+  int* counts = nullptr;  // [nq][splits] valid keys per list (null: lists padded with kNoKey)
 };
+constexpr int kMaxMergeLists = 1024;  // lists per query when counts are given
 
 int fp32_scan_grid(const DeviceStore& st, int qb, int sm_count);
 size_t fp32_scan_cand_bytes(int grid, int qb, int k1);
@@ -97,7 +99,8 @@ int small_grid(int64_t n_rows, int sm_count);
 // the k best (first level) or re-rank the k1 with both levels and write k.
 cudaError_t launch_merge_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                                 const uint64_t* partial, int splits, int k1, int k, bool rerank,
-                                int64_t* out_ids, float* out_scores, cudaStream_t stream);
+                                int64_t* out_ids, float* out_scores, cudaStream_t stream,
+                                const int* counts = nullptr, int sm_count = 0);
 cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                           const int64_t* ids, int k1, int k, int64_t* out_ids, float* out_scores,
                           cudaStream_t stream);

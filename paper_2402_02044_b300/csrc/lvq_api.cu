@@ -170,6 +170,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, S
   sc.plan.n_rows = n_rows;
   sc.plan.k1 = k1;
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
+  sc.plan.counts = path == kPathSmall ? c.take<int>((size_t)nq * splits) : nullptr;
   const size_t cand = mma                  ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
                      : path == kPathSmall ? 0
                                           : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);
@@ -249,7 +250,7 @@ lvq_status first_level(lvq_store* s, const float* q, int64_t nq, int k1, int k, 
   {
     Prof p(s, stream, LVQ_K_MERGE);
     e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, k1, k, rerank, out_ids,
-                            out_scores, stream);
+                            out_scores, stream, sc.plan.counts, s->sm_count);
   }
   if (e != cudaSuccess) return cuda_fail(s, e, "merge_rerank");
   return LVQ_OK;
@@ -519,7 +520,8 @@ lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int
   if (e != cudaSuccess) return cuda_fail(s, e, "prep_queries");
   e = launch_scan_small(st, nq, sc.prep, sc.small, sc.plan, str);
   if (e != cudaSuccess) return cuda_fail(s, e, "scan_small");
-  e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, kk1, k, two, out_ids, out_scores, str);
+  e = launch_merge_rerank(st, q, nq, sc.prep, sc.plan.partial, sc.plan.splits, kk1, k, two, out_ids, out_scores, str,
+                          sc.plan.counts, s->sm_count);
   if (e != cudaSuccess) return cuda_fail(s, e, "merge_rerank");
   return LVQ_OK;
 }

@@ -341,6 +341,15 @@ __device__ __forceinline__ RowMeta load_meta(const MmaArgs& a, int64_t rw, bool 
 
 // CM: how <q, mu_m> of the query tile is held in shared memory: 0 not at
 // all, 1 float16, 2 float32.
+// Candidate-buffer selections, kept out of line: they run rarely and their
+// register arrays would otherwise share the epilogue's register budget.
+__device__ __noinline__ int prune_keys(uint64_t* buf, int n, int k, int keep_max, int* hist, uint64_t* thr) {
+  return warp_prune(buf, n, k, keep_max, hist, thr);
+}
+__device__ __noinline__ int select_keys(uint64_t* buf, int n, int k, int* hist, uint64_t* thr) {
+  return warp_select6(buf, n, k, hist, thr);
+}
+
 template <int N, int BITS, int CM>
 __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, int warp, int lane) {
   const int quarter = warp & 3;
@@ -471,12 +480,18 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       ++di;
       named_bar(1, kEpiThreads);
       if (ew < 4) {
-        // warps 0-3 compact the buffers that may not take another tile
-        for (int n = ew; n < N; n += 4) {
+        // warps 0-3 compact the buffers that may not take another tile: warp
+        // ew owns queries ew, ew + 4, ... (one per lane, N <= 128), and only
+        // those whose buffer is full are visited
+        const int nl = ew + 4 * lane;
+        uint32_t full = __ballot_sync(kFull, nl < N && __float_as_int(c.fq[nl < N ? nl : 0].w) > a.cap - kRows);
+        while (full) {
+          const int n = ew + 4 * (__ffs((int)full) - 1);
+          full &= full - 1;
           const int cnt = __float_as_int(c.fq[n].w);
-          if (cnt > a.cap - kRows) {
+          {
             uint64_t tk;
-            const int kept = warp_prune(mybuf + n * a.cap, cnt, a.k1, a.k1 + (a.cap - kRows - a.k1) / 2, myhist, &tk);
+            const int kept = prune_keys(mybuf + n * a.cap, cnt, a.k1, a.k1 + (a.cap - kRows - a.k1) / 2, myhist, &tk);
             if (lane == 0) {
               c.fq[n].w = __int_as_float(kept);
               c.thr[n] = tk;
@@ -506,7 +521,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
         for (int n = ew; n < N; n += 4) {
           if (q0 + n >= a.nq) continue;
           uint64_t tk;
-          const int kept = warp_select6(mybuf + n * a.cap, __float_as_int(c.fq[n].w), a.k1, myhist, &tk);
+          const int kept = select_keys(mybuf + n * a.cap, __float_as_int(c.fq[n].w), a.k1, myhist, &tk);
           uint64_t* dst = a.partial + ((q0 + n) * a.seg_max + seg) * a.k1;
           for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? mybuf[n * a.cap + i] : kNoKey;
         }

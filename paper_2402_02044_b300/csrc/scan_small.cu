@@ -54,6 +54,8 @@ struct SmallArgs {
   int k1, cap;
   int64_t n_rows, ntiles;
   uint64_t* partial;    // [nq][gridDim.x][k1]
+  int* counts;          // [nq][gridDim.x] keys written per list
+  uint64_t* gthr;       // [nq] lowest k1-th key any CTA has found (bounds the global k1-th)
 };
 
 __device__ __forceinline__ int dp4a_us(uint32_t a, uint32_t b, int c) {
@@ -216,6 +218,9 @@ __global__ void __launch_bounds__(small_threads(G), 1)
     uint32_t used = 0;              // boxes taken from this group's ring
     bool go = true;
     for (int64_t t = t_begin + g; t < t_end; t += G) {
+      // the global bound as of this tile's start, read now and used after it
+      uint64_t gt_tile = kNoKey;
+      if (wq < QB && wq < a.nq && lane == 0) gt_tile = *reinterpret_cast<volatile uint64_t*>(a.gthr + wq);
       if (go) {
         // four independent accumulator chains per query: A/B halves (4-bit)
         // or even/odd words (8-bit), high and low query bytes
@@ -309,14 +314,20 @@ __global__ void __launch_bounds__(small_threads(G), 1)
       }
       named_bar(1 + g, 128);
       go = go && !*abort_sh;
-      // a buffer without room for another tile is cut to the k1 best
-      if (wq < QB && wq < a.nq && my_cnt[wq] > cap - kRows) {
-        uint64_t tk;
-        const int kept = select_k(cand + (wq * G + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
-        if (lane == 0) {
-          my_cnt[wq] = kept;
-          my_thr[wq] = tk;
+      if (wq < QB && wq < a.nq) {
+        // a buffer without room for another tile is cut to the k1 best, whose
+        // k1-th key bounds every CTA's search
+        if (my_cnt[wq] > cap - kRows) {
+          uint64_t tk;
+          const int kept = select_k(cand + (wq * G + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
+          if (lane == 0) {
+            my_cnt[wq] = kept;
+            if (tk < my_thr[wq]) my_thr[wq] = tk;
+            if (tk != kNoKey) atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + wq), tk);
+          }
+          __syncwarp();
         }
+        if (lane == 0 && gt_tile < my_thr[wq]) my_thr[wq] = gt_tile;
         __syncwarp();
       }
       named_bar(1 + g, 128);
@@ -340,8 +351,20 @@ __global__ void __launch_bounds__(small_threads(G), 1)
       }
       uint64_t tk;
       const int kept = select_k(b0, n, a.k1, hist + cw * 64, &tk);
+      if (lane == 0 && kept == a.k1) atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + q), tk);
+      __syncwarp();
+      // only keys at or below the global bound can be among the k1 best
+      const uint64_t gt = *reinterpret_cast<volatile uint64_t*>(a.gthr + q);
       uint64_t* dst = a.partial + ((int64_t)q * gridDim.x + blockIdx.x) * a.k1;
-      for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? b0[i] : kNoKey;
+      int pos = 0;
+      for (int base = 0; base < kept; base += 32) {
+        const uint64_t v = base + lane < kept ? b0[base + lane] : kNoKey;
+        const bool keep = base + lane < kept && v <= gt;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) dst[pos + __popc(m & ((1u << lane) - 1u))] = v;
+        pos += __popc(m);
+      }
+      if (lane == 0) a.counts[(int64_t)q * gridDim.x + blockIdx.x] = pos;
     }
   }
 }
@@ -350,7 +373,7 @@ __global__ void __launch_bounds__(small_threads(G), 1)
 // order (one warp per query).
 __global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
                                                          int Wp, uint32_t* __restrict__ qw,
-                                                         float* __restrict__ qscale) {
+                                                         float* __restrict__ qscale, uint64_t* __restrict__ gthr) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= nq) return;
@@ -362,7 +385,10 @@ __global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const f
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const float s = mx > 0.0f ? mx / 32767.0f : 1.0f;
   const float inv = mx > 0.0f ? 32767.0f / mx : 0.0f;
-  if (lane == 0) qscale[i] = s;
+  if (lane == 0) {
+    qscale[i] = s;
+    gthr[i] = kNoKey;
+  }
   uint32_t* out = qw + i * 4 * Wp;
   auto qint = [&](int j) -> int {
     return j < d ? max(-32767, min(32767, __float2int_rn(qi[j] * inv))) : 0;
@@ -410,9 +436,9 @@ cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_
 int small_cap(int k1) { return pow2_at_least(k1 + 2 * kRows); }
 int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
 int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
-// consumer groups: three for one or two queries (more warps to hide the
-// latency of the loads), two for up to four (registers of four queries)
-int small_groups(int qb) { return qb <= 2 ? 3 : 2; }
+// consumer groups: more warps hide more load latency, while the registers of
+// more queries allow fewer of them (4, 3 and 2 groups for 1, 2 and 4 slots)
+int small_groups(int qb) { return qb <= 1 ? 4 : qb <= 2 ? 3 : 2; }
 
 // ring stages per ring: as many as shared memory holds, up to kMaxRingStages;
 // 0 when not even two fit
@@ -432,8 +458,13 @@ bool small_supported(const DeviceStore& st, int64_t nq, int k1) {
   return small_stages(st, small_qb(nq), k1) > 0;
 }
 
+// scratch: rounded queries [nq][4][Wp] u32 | scales [nq] f32 | global bounds [nq] u64 (8-byte aligned)
 size_t small_scratch_bytes(const DeviceStore& st, int64_t nq) {
-  return (size_t)nq * 4 * small_wp(st) * 4 + (size_t)nq * 4 + 256;
+  return (size_t)nq * 4 * small_wp(st) * 4 + (size_t)nq * 8 + (size_t)nq * 8 + 256;
+}
+static uint64_t* small_gthr(void* scratch, const DeviceStore& st, int64_t nq) {
+  const size_t off = (size_t)nq * 4 * small_wp(st) * 4 + (size_t)nq * 8;
+  return reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + off);
 }
 
 int small_grid(int64_t n_rows, int sm_count) {
@@ -446,7 +477,8 @@ cudaError_t launch_small_prep(const DeviceStore& st, const float* q, int64_t nq,
   const int Wp = small_wp(st);
   uint32_t* qw = reinterpret_cast<uint32_t*>(scratch);
   float* qscale = reinterpret_cast<float*>(qw + nq * 4 * Wp);
-  small_prep_kernel<<<(unsigned)ceil_div(nq, 8), 256, 0, stream>>>(st, q, nq, Wp, qw, qscale);
+  small_prep_kernel<<<(unsigned)ceil_div(nq, 8), 256, 0, stream>>>(st, q, nq, Wp, qw, qscale,
+                                                                     small_gthr(scratch, st, nq));
   return cudaGetLastError();
 }
 
@@ -468,6 +500,9 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
   a.n_rows = plan.n_rows;
   a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, kRows);
   a.partial = plan.partial;
+  a.counts = plan.counts;
+  a.gthr = small_gthr(const_cast<void*>(scratch), st, nq);
+  if (!a.counts) return cudaErrorInvalidValue;
   const int qb = small_qb(nq);
   a.stages = small_stages(st, qb, plan.k1);
   if (a.stages == 0) return cudaErrorInvalidValue;
@@ -478,7 +513,7 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
   const int grid = plan.grid;
   const bool b4 = st.bits1 == 4;
   switch (qb) {
-    case 1: return b4 ? launch_qb<1, 4, 3>(cm, a, grid, smem, stream) : launch_qb<1, 8, 3>(cm, a, grid, smem, stream);
+    case 1: return b4 ? launch_qb<1, 4, 4>(cm, a, grid, smem, stream) : launch_qb<1, 8, 4>(cm, a, grid, smem, stream);
     case 2: return b4 ? launch_qb<2, 4, 3>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3>(cm, a, grid, smem, stream);
     default: return b4 ? launch_qb<4, 4, 2>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2>(cm, a, grid, smem, stream);
   }

@@ -82,14 +82,16 @@ __device__ void rerank_tail(const DeviceStore& st, const float* qsh, const uint6
 }
 
 // ---- merge of per-split lists + optional re-rank (one block per query) --------
-constexpr int kMergeThreads = 128;
-constexpr int kMergePer = 8;
-constexpr int kMergeRound = kMergeThreads * kMergePer;
+// T threads per block (128, or 512 when there are fewer queries than SMs, so
+// that a lone query's re-rank has more warps); rounds of kMergeRound keys.
+constexpr int kMergeRound = 1024;
 
-__global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore st, const float* __restrict__ q,
-                                                                      const uint64_t* __restrict__ partial,
-                                                                      int splits, int k1, int k, int rerank,
-                                                                      int64_t* out_ids, float* out_scores) {
+template <int T>
+__global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const float* __restrict__ q,
+                                                         const uint64_t* __restrict__ partial,
+                                                         const int* __restrict__ counts, int splits, int k1, int k,
+                                                         int rerank, int64_t* out_ids, float* out_scores) {
+  constexpr int kMergePer = kMergeRound / T;
   extern __shared__ __align__(16) unsigned char smem[];
   const int qi = blockIdx.x;
   const int cap = pow2_at_least(k1 + kMergeRound);
@@ -100,22 +102,28 @@ __global__ void __launch_bounds__(kMergeThreads) merge_rerank_kernel(DeviceStore
   __shared__ int cnt;
   __shared__ uint64_t thr;
   __shared__ int hist[288];
+  __shared__ int len[kMaxMergeLists];  // valid keys per list (counts given)
   if (threadIdx.x == 0) {
     cnt = 0;
     thr = kNoKey;
   }
   for (int j = threadIdx.x; j < st.d; j += blockDim.x) qsh[j] = q[(int64_t)qi * st.d + j];
+  if (counts)
+    for (int i = threadIdx.x; i < splits; i += blockDim.x) len[i] = counts[(int64_t)qi * splits + i];
   __syncthreads();
   const uint64_t* src = partial + (int64_t)qi * splits * k1;
   const int total = splits * k1;
   const int lane = threadIdx.x & 31;
-  // rounds of kMergeRound keys, kMergePer independent loads per thread
+  // rounds of kMergeRound keys, kMergePer independent loads per thread; with
+  // counts, positions past a list's length are not read
   for (int base = 0; base < total; base += kMergeRound) {
     uint64_t v[kMergePer];
 #pragma unroll
     for (int r = 0; r < kMergePer; ++r) {
-      const int i = base + r * kMergeThreads + threadIdx.x;
-      v[r] = i < total ? __ldg(src + i) : kNoKey;
+      const int i = base + r * T + threadIdx.x;
+      bool in = i < total;
+      if (in && counts) in = (i % k1) < len[i / k1];
+      v[r] = in ? __ldg(src + i) : kNoKey;
     }
     const uint64_t t = thr;
 #pragma unroll
@@ -303,6 +311,20 @@ cudaError_t launch_prep_queries(const DeviceStore& st, const float* q, int64_t n
   return cudaGetLastError();
 }
 
+template <int T>
+cudaError_t launch_merge_t(const DeviceStore& st, const float* q, int64_t nq, const uint64_t* partial,
+                           const int* counts, int splits, int k1, int k, bool rerank, int64_t* out_ids,
+                           float* out_scores, size_t sm, cudaStream_t stream) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(merge_rerank_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  merge_rerank_kernel<T><<<(unsigned)nq, T, sm, stream>>>(st, q, partial, counts, splits, k1, k, rerank ? 1 : 0,
+                                                          out_ids, out_scores);
+  return cudaGetLastError();
+}
+
 static size_t merge_smem(int d, int k1) {
   return (size_t)(pow2_at_least(k1 + kMergeRound) + pow2_at_least(k1)) * 8 + (size_t)d * 4 +
          (size_t)(k1 + 2) * 4 + 16;
@@ -310,17 +332,14 @@ static size_t merge_smem(int d, int k1) {
 
 cudaError_t launch_merge_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep&,
                                 const uint64_t* partial, int splits, int k1, int k, bool rerank,
-                                int64_t* out_ids, float* out_scores, cudaStream_t stream) {
+                                int64_t* out_ids, float* out_scores, cudaStream_t stream, const int* counts,
+                                int sm_count) {
   if (nq <= 0) return cudaSuccess;
+  if (counts && splits > kMaxMergeLists) return cudaErrorInvalidValue;
   const size_t sm = merge_smem(st.d, k1 > k ? k1 : k);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(merge_rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
-  merge_rerank_kernel<<<(unsigned)nq, kMergeThreads, sm, stream>>>(st, q, partial, splits, k1, k, rerank ? 1 : 0,
-                                                                   out_ids, out_scores);
-  return cudaGetLastError();
+  if (nq < sm_count)
+    return launch_merge_t<512>(st, q, nq, partial, counts, splits, k1, k, rerank, out_ids, out_scores, sm, stream);
+  return launch_merge_t<128>(st, q, nq, partial, counts, splits, k1, k, rerank, out_ids, out_scores, sm, stream);
 }
 
 cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep&, const int64_t* ids,

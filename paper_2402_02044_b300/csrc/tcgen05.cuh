@@ -183,6 +183,23 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[LEN]) 
       : "r"(taddr)
       : "memory");
 }
+template <int OFF, int LEN>
+__device__ __forceinline__ void tmem_ld_x8(uint32_t taddr, uint32_t (&r)[LEN]) {
+  static_assert(OFF + 8 <= LEN, "range");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[OFF + 0]), "=r"(r[OFF + 1]), "=r"(r[OFF + 2]), "=r"(r[OFF + 3]), "=r"(r[OFF + 4]),
+                 "=r"(r[OFF + 5]), "=r"(r[OFF + 6]), "=r"(r[OFF + 7])
+               : "r"(taddr)
+               : "memory");
+}
+template <int OFF, int LEN>
+__device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, uint32_t (&r)[LEN]) {
+  static_assert(OFF + 4 <= LEN, "range");
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[OFF + 0]), "=r"(r[OFF + 1]), "=r"(r[OFF + 2]), "=r"(r[OFF + 3])
+               : "r"(taddr)
+               : "memory");
+}
 // one column starting at taddr (one 32-bit value per lane)
 __device__ __forceinline__ uint32_t tmem_ld_x1(uint32_t taddr) {
   uint32_t r;
