@@ -63,6 +63,7 @@ struct ScanPlan {
   uint64_t* cand;       // per-CTA candidate buffers
   int grid;             // persistent CTAs
   int* counts = nullptr;  // [nq][splits] valid keys per list (null: lists padded with kNoKey)
+  uint64_t* gthr = nullptr;  // [nq] per-query bound shared by the CTAs of the tensor-core scan
 };
 constexpr int kMaxMergeLists = 1024;  // lists per query when counts are given
 
@@ -80,7 +81,8 @@ bool mma_supported(const DeviceStore& st);
 // swizzle, 128: 128-byte swizzle)
 cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm, int box_bytes);
 int mma_tile_limit(const DeviceStore& st);   // largest query tile whose queries fit in shared memory
-int mma_seg_max(int grid, int64_t groups);   // segments per query tile in the partial lists
+// database segments per query tile: groups x segments is a multiple of grid
+int mma_segments(int grid, int64_t groups, int64_t ntiles);   // segments per query tile in the partial lists
 
 // small-batch integer scan (scan_small.cu): queries quantised to 16-bit
 // integers (hi and lo bytes), codes as bytes, dp4a dot products on CUDA cores

@@ -147,14 +147,12 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, S
   const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, tiles_rows);
   int splits;
   if (mma) {
-    // (query tile, database tile) units are shared evenly by the CTAs; a
-    // query tile is cut into at most seg_max segments
-    const int64_t units = groups * ntiles;
+    // jobs (query tile x database segment) dealt round-robin to the CTAs
     int g = s->tuning.mma_ctas > 0 ? s->tuning.mma_ctas : grid;
-    if (g > units) g = (int)units;
     if (g < 1) g = 1;
-    sc.plan.grid = g;
-    splits = mma_seg_max(g, groups);
+    splits = mma_segments(g, groups, ntiles);
+    const int64_t jobs = groups * splits;
+    sc.plan.grid = (int)(jobs < g ? jobs : g);
   } else if (path == kPathSmall) {
     // one contiguous range of tiles per CTA; each CTA writes its own list
     sc.plan.grid = grid;
@@ -170,7 +168,8 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, S
   sc.plan.n_rows = n_rows;
   sc.plan.k1 = k1;
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
-  sc.plan.counts = path == kPathSmall ? c.take<int>((size_t)nq * splits) : nullptr;
+  sc.plan.counts = path != kPathFp32 ? c.take<int>((size_t)nq * splits) : nullptr;
+  sc.plan.gthr = mma ? c.take<uint64_t>((size_t)nq) : nullptr;
   const size_t cand = mma                  ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
                      : path == kPathSmall ? 0
                                           : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);

@@ -25,7 +25,7 @@
 //               (double buffered in TMEM) 16 columns at a time, a cheap
 //               per-query filter, then the exact key and the top-k1
 //               threshold test for the few rows that pass it.
-// Work is the list of (query tile, database tile) units, split evenly
+// Work is a list of jobs (a query tile x a database segment), dealt evenly
 // between the CTAs; a CTA's stretch of one query tile is a "segment" whose
 // k1 best keys go to partial[q][segment].
 //
@@ -65,7 +65,9 @@ struct MmaArgs {
   QueryPrep p;
   int k1;
   int64_t n_rows;
-  uint64_t* partial;  // [nq][seg_max][k1]
+  uint64_t* partial;  // [nq][segs][k1]: keys of each (query, database segment)
+  int* counts;        // [nq][segs] keys written per list
+  uint64_t* gthr;     // [nq] lowest k1-th key any job has found (bounds the global k1-th)
   uint64_t* cand;     // [grid][N][cap]
   int cap;
   int n_kbox;         // code boxes per row
@@ -73,8 +75,9 @@ struct MmaArgs {
   int a_stages;       // depth of the A ring in TMEM
   int code_stages;    // depth of the code-box ring in shared memory
   int64_t ntiles;     // database tiles
-  int64_t units;      // query tiles x database tiles
-  int seg_max;
+  int64_t groups;     // query tiles
+  int segs;           // database segments (equal ranges of tiles)
+  int64_t jobs;       // groups x segs; job j = (query tile j % groups, segment j / groups)
 };
 
 struct Smem {
@@ -113,11 +116,20 @@ __device__ __forceinline__ Bars bars_at(uint64_t* b) {
   return r;
 }
 
-__device__ __forceinline__ int64_t unit_begin(int64_t units, int c, int grid) { return units * c / grid; }
-
-// first CTA whose stretch of units contains unit u
-__device__ __forceinline__ int cta_of_unit(int64_t u, int64_t units, int grid) {
-  return (int)(((u + 1) * grid - 1) / units);
+// Jobs are dealt round-robin: CTA c takes jobs c, c + grid, ...  At any time
+// the CTAs then work on one or two neighbouring database segments for many
+// query tiles, so a code tile read from HBM is reused from L2.
+struct Job {
+  int64_t g, t0, t1;  // query tile, database tiles [t0, t1)
+  int s;              // segment
+};
+__device__ __forceinline__ Job job_of(const MmaArgs& a, int64_t j) {
+  Job r;
+  r.g = j % a.groups;
+  r.s = (int)(j / a.groups);
+  r.t0 = a.ntiles * r.s / a.segs;
+  r.t1 = a.ntiles * (r.s + 1) / a.segs;
+  return r;
 }
 
 // float16 pairs of half of a 64-byte box of a row (32 bytes, chunks 2h and
@@ -161,7 +173,6 @@ struct Ctx {
   __half* cm16;     // [N][M] <q, mu_m> in float16, or null
   float* cm32;      // [N][M] <q, mu_m> in float32, or null
   volatile int* ep_go;  // [2] epilogue leader's verdicts, read by the 4 epilogue warps after a named barrier
-  int64_t u_begin, u_end;
   int cta, grid;
 };
 
@@ -181,9 +192,9 @@ __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUt
                                               const Ctx& c) {
   uint32_t ci = 0, qi = 0;
   int64_t g_cur = -1;
-  for (int64_t u = c.u_begin; u < c.u_end && !*c.abort_sh;) {
-    const int64_t g = u / a.ntiles, t0 = u % a.ntiles;
-    const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
+  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+    const Job jb = job_of(a, j);
+    const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     if (g != g_cur) {
       if (qi > 0) LVQ_WAIT(c, c.B.q_empty, (qi - 1) & 1);
       mbar_expect_tx(c.B.q_full, (uint32_t)(a.qboxes * N * 128));
@@ -201,7 +212,6 @@ __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUt
         ++ci;
       }
     }
-    u += t1 - t0;
   }
 out:
   // copies that may still be in flight: the last (up to) 3 code boxes and
@@ -223,9 +233,9 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
   uint32_t ai = 0, di = 0, qi = 0;
   int64_t g_cur = -1;
   const uint32_t qbase = smem_u32(c.qs);
-  for (int64_t u = c.u_begin; u < c.u_end && !*c.abort_sh;) {
-    const int64_t g = u / a.ntiles, t0 = u % a.ntiles;
-    const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
+  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+    const Job jb = job_of(a, j);
+    const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     if (g != g_cur) {
       LVQ_WAIT(c, c.B.q_full, qi & 1);
       ++qi;
@@ -256,7 +266,6 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
       mma_commit(c.B.d_full + db);
       ++di;
     }
-    u += t1 - t0;
     mma_commit(c.B.q_empty);
   }
 out:
@@ -274,9 +283,9 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
   const int row = quarter * 32 + lane;
   const uint32_t lane_base = c.tbase + ((uint32_t)(quarter * 32) << 16);
   uint32_t ci = 0, ai = 0;  // boxes seen by the CTA so far
-  for (int64_t u = c.u_begin; u < c.u_end && !*c.abort_sh;) {
-    const int64_t t0 = u % a.ntiles;
-    const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
+  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+    const Job jb = job_of(a, j);
+    const int64_t t0 = jb.t0, t1 = jb.t1;
     for (int64_t t = t0; t < t1; ++t) {
       for (int kb = 0; kb < a.n_kbox; ++kb, ++ci, ++ai) {
         const int s = ci % a.code_stages;
@@ -288,22 +297,19 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         for (int q = 0; q < 4; ++q) w[q] = src[q ^ sw];
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.code_empty + s);
+        // both halves in their own registers: tcgen05.st reads its source
+        // registers after issue, so none is rewritten before the wait
+        uint32_t r[32], r2[32];
+        unpack_half<BITS>(w, 0, r);
+        unpack_half<BITS>(w, 1, r2);
         const int as = ai % AS;
         LVQ_WAIT(c, c.B.a_empty + as, ((ai / AS) & 1) ^ 1);
         tc_fence_after();
         const uint32_t taddr = lane_base + 2 * N + as * kACols;
         if (BITS == 4) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[32];
-            unpack_half<BITS>(w, h, r);
-            tmem_st_x32<0>(taddr + 32 * h, r);
-          }
+          tmem_st_x32<0>(taddr, r);
+          tmem_st_x32<0>(taddr + 32, r2);
         } else {
-          uint32_t r[32];
-          unpack_half<BITS>(w, 0, r);
-          uint32_t r2[32];
-          unpack_half<BITS>(w, 1, r2);
 #pragma unroll
           for (int i = 0; i < 16; ++i) r[16 + i] = r2[i];
           tmem_st_x32<0>(taddr, r);
@@ -314,7 +320,6 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         if (lane == 0) mbar_arrive(c.B.a_full + as);
       }
     }
-    u += t1 - t0;
   }
 out:
   return;
@@ -341,6 +346,17 @@ __device__ __forceinline__ RowMeta load_meta(const MmaArgs& a, int64_t rw, bool 
 
 // CM: how <q, mu_m> of the query tile is held in shared memory: 0 not at
 // all, 1 float16, 2 float32.
+// A threshold key's score as a bound on the filter value (plus <q, mu_m>
+// when the table is held; less max |<q, mu_m>| when not), less a margin for
+// rounding.
+__device__ __forceinline__ float bound_of(uint64_t tk, float qn, float cmabs, bool ip, int cm_table) {
+  const float ts = key_score(tk, ip ? LVQ_IP : LVQ_L2);
+  float b = ip ? ts : 0.5f * (qn - ts);
+  b -= 1e-5f * (fabsf(ts) + qn + cmabs) + 1e-30f;
+  if (cm_table == 0) b -= cmabs;
+  return b;
+}
+
 // Candidate-buffer selections, kept out of line: they run rarely and their
 // register arrays would otherwise share the epilogue's register budget.
 __device__ __noinline__ int prune_keys(uint64_t* buf, int n, int k, int keep_max, int* hist, uint64_t* thr) {
@@ -372,21 +388,25 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
   // flag, and publishes its verdict in shared memory before a barrier.
   // Verdicts alternate between two slots, so a slot is rewritten only after
   // every warp has passed the barrier that follows its read.
-  for (int64_t u = c.u_begin; u < c.u_end;) {
-    const int64_t g = u / a.ntiles, t0 = u % a.ntiles;
-    const int64_t t1 = min(a.ntiles, t0 + (c.u_end - u));
+  for (int64_t j = c.cta; j < a.jobs; j += c.grid) {
+    const Job jb = job_of(a, j);
+    const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     const int64_t q0 = g * N;
     if (et < N) {
       const bool real = q0 + et < a.nq;
-      c.thr[et] = real ? kNoKey : 0ull;
       float cmabs = 0.0f;
       if (real)
         for (int m = 0; m < st.n_means; ++m) cmabs = fmaxf(cmabs, fabsf(a.p.cm[(q0 + et) * st.n_means + m]));
       c.cmabs_s[et] = cmabs;
-      c.qnorm_s[et] = real ? a.p.qnorm[q0 + et] : 0.0f;
-      // absent queries take nothing (bound +inf), real ones everything (-inf)
-      c.fq[et] = make_float4(real ? a.p.qsum[q0 + et] : 0.0f, real ? 1024.0f * a.p.q16sum[q0 + et] : 0.0f,
-                             real ? __int_as_float(0xff800000) : __int_as_float(0x7f800000), 0.0f);
+      const float qn = real ? a.p.qnorm[q0 + et] : 0.0f;
+      c.qnorm_s[et] = qn;
+      // absent queries take nothing (bound +inf); real ones start from the
+      // global bound of earlier jobs (everything, -inf, while there is none)
+      const uint64_t gt = real ? *reinterpret_cast<volatile uint64_t*>(a.gthr + q0 + et) : 0ull;
+      c.thr[et] = gt;
+      float b = real ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+      if (real && gt != kNoKey) b = bound_of(gt, qn, cmabs, ip, CM);
+      c.fq[et] = make_float4(real ? a.p.qsum[q0 + et] : 0.0f, real ? 1024.0f * a.p.q16sum[q0 + et] : 0.0f, b, 0.0f);
     }
     if (CM) {
       for (int i = et; i < N * st.n_means; i += kEpiThreads) {
@@ -496,14 +516,8 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
               c.fq[n].w = __int_as_float(kept);
               c.thr[n] = tk;
               if (tk != kNoKey) {
-                // the new threshold score as a bound on the filter value (plus
-                // <q, mu_m>), less a margin for rounding
-                const float ts = key_score(tk, st.metric);
-                const float qn = c.qnorm_s[n];
-                float b = ip ? ts : 0.5f * (qn - ts);
-                b -= 1e-5f * (fabsf(ts) + qn + c.cmabs_s[n]) + 1e-30f;
-                if (CM == 0) b -= c.cmabs_s[n];
-                c.fq[n].z = b;
+                atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + q0 + n), tk);
+                c.fq[n].z = bound_of(tk, c.qnorm_s[n], c.cmabs_s[n], ip, CM);
               }
             }
             __syncwarp();
@@ -513,22 +527,29 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       named_bar(1, kEpiThreads);
     }
     if (ew < 4) {
-      // end of this CTA's segment of query tile g: k1 best of each query
-      const int seg = c.cta - cta_of_unit(g * a.ntiles, a.units, c.grid);
-      if (seg < 0 || seg >= a.seg_max) {
-        if (et == 0) set_error(st.err, LVQ_ECUDA);
-      } else {
-        for (int n = ew; n < N; n += 4) {
-          if (q0 + n >= a.nq) continue;
-          uint64_t tk;
-          const int kept = select_keys(mybuf + n * a.cap, __float_as_int(c.fq[n].w), a.k1, myhist, &tk);
-          uint64_t* dst = a.partial + ((q0 + n) * a.seg_max + seg) * a.k1;
-          for (int i = lane; i < a.k1; i += 32) dst[i] = i < kept ? mybuf[n * a.cap + i] : kNoKey;
+      // end of job: the k1 best of each query in segment jb.s; its k1-th key
+      // bounds every job, and only keys at or below the bound are kept
+      for (int n = ew; n < N; n += 4) {
+        if (q0 + n >= a.nq) continue;
+        uint64_t tk;
+        uint64_t* b0 = mybuf + n * a.cap;
+        const int kept = select_keys(b0, __float_as_int(c.fq[n].w), a.k1, myhist, &tk);
+        if (lane == 0 && kept == a.k1) atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + q0 + n), tk);
+        __syncwarp();
+        const uint64_t gt = *reinterpret_cast<volatile uint64_t*>(a.gthr + q0 + n);
+        uint64_t* dst = a.partial + ((q0 + n) * a.segs + jb.s) * a.k1;
+        int pos = 0;
+        for (int base = 0; base < kept; base += 32) {
+          const uint64_t v = base + lane < kept ? b0[base + lane] : kNoKey;
+          const bool keep = base + lane < kept && v <= gt;
+          const unsigned m = __ballot_sync(kFull, keep);
+          if (keep) dst[pos + __popc(m & ((1u << lane) - 1u))] = v;
+          pos += __popc(m);
         }
+        if (lane == 0) a.counts[(q0 + n) * a.segs + jb.s] = pos;
       }
     }
     named_bar(1, kEpiThreads);
-    u += t1 - t0;
   }
 out:
   return;
@@ -560,8 +581,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.B = bars_at(bar_mem);
   c.grid = gridDim.x;
   c.cta = blockIdx.x;
-  c.u_begin = unit_begin(a.units, c.cta, c.grid);
-  c.u_end = unit_begin(a.units, c.cta + 1, c.grid);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -700,7 +719,18 @@ int mma_tile_limit(const DeviceStore& st) { return max_n_tile(st); }
 
 size_t mma_scan_cand_bytes(int grid, int n_tile, int k1) { return (size_t)grid * n_tile * mma_cap(k1) * 8; }
 
-int mma_seg_max(int grid, int64_t groups) { return (int)ceil_div(grid, groups) + 1; }
+int mma_segments(int grid, int64_t groups, int64_t ntiles) {
+  // groups x segments a multiple of grid: every CTA gets as many jobs
+  int64_t x = groups, y = grid;
+  while (y) {
+    const int64_t t = x % y;
+    x = y;
+    y = t;
+  }
+  int64_t segs = grid / x;
+  if (segs > ntiles) segs = ntiles;
+  return (int)(segs < 1 ? 1 : segs);
+}
 
 cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& p, int n_tile, const ScanPlan& plan,
                             cudaStream_t stream) {
@@ -723,10 +753,13 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   a.a_stages = (kTmemCols - 2 * n_tile) / acols;
   if (a.a_stages > 8) a.a_stages = 8;
   a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, kRows);
-  const int64_t groups = p.nq_pad / n_tile;
-  a.units = groups * a.ntiles;
+  a.groups = p.nq_pad / n_tile;
+  a.segs = plan.splits;
+  a.jobs = a.groups * a.segs;
+  a.counts = plan.counts;
+  a.gthr = plan.gthr;
+  if (!a.counts || !a.gthr || a.segs < 1 || a.segs > a.ntiles) return cudaErrorInvalidValue;
   const int grid = plan.grid;
-  a.seg_max = plan.splits;
 
   CUtensorMap cm, qm;
   {
@@ -743,7 +776,7 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaMemsetAsync(plan.partial, 0xFF, (size_t)nq * a.seg_max * plan.k1 * 8, stream);
+  cudaError_t e = cudaMemsetAsync(plan.gthr, 0xFF, (size_t)nq * 8, stream);
   if (e != cudaSuccess) return e;
   // as many code stages as shared memory allows (more bytes in flight for
   // narrow query tiles)

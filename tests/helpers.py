@@ -125,3 +125,10 @@ def check_two_level(q, gpu_ids, enc, means, metric, k1, k, tol, live=None, cand_
             # reverse: a near-tie at the final boundary, or its first-level
             # score sits at the k1 boundary (in or out of the candidate set)
             assert tie2 or tie1 or (g not in in_k1 and tie1), (i, g)
+
+
+def check_no_device_error(st):
+    """No bounded device wait expired and no other sticky error was recorded."""
+    from paper_2402_02044_b300 import lvq as L
+    code, msg = L.lvq_last_error(st.handle)
+    assert code == 0, msg

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import (TOL_FP16, TOL_FP32, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
+from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
                      lib_store)
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +54,7 @@ def test_tensor_core_first_level_and_search(case):
     # re-rank distances are float32
     check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
     check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    check_no_device_error(st)
     st.close()
 
 
@@ -71,6 +72,7 @@ def test_every_tile_width_gives_the_same_candidates(mma_n):
     st.set_tuning(mma_n=mma_n, mma_ctas=7)
     fi2, fs2 = st.first_level(qt, 64, "fp16")
     assert torch.equal(fi, fi2) and torch.equal(fs, fs2)
+    check_no_device_error(st)
     st.close()
 
 
@@ -92,6 +94,7 @@ def test_tensor_core_respects_deletes_and_padding():
     gi, gs = st.search(qt, 10, 40, "fp16")
     gi = gi.cpu().numpy()
     assert np.all(np.sort(gi[:, :2], axis=1) == keep) and np.all(gi[:, 2:] == -1)
+    check_no_device_error(st)
     st.close()
 
 
@@ -103,4 +106,5 @@ def test_fp16_and_fp32_paths_agree():
     b_i, b_s = st.search(qt, 10, 100, "fp32")
     agree = np.mean([len(set(r1) & set(r2)) / 10 for r1, r2 in zip(a_i.cpu().numpy(), b_i.cpu().numpy())])
     assert agree >= 0.999
+    check_no_device_error(st)
     st.close()

@@ -16,7 +16,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import (TOL_FP16, TOL_FP32, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
+from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
                      lib_store)
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +57,7 @@ def test_integer_first_level_and_search(case):
     check_sorted(gs, metric)
     check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
     check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    check_no_device_error(st)
     st.close()
 
 
@@ -84,6 +85,7 @@ def test_auto_takes_the_integer_scan_for_small_batches():
     g_i, _ = st.search(qt[:4], 10, 100, "int16")
     agree = np.mean([len(set(r1) & set(r2)) / 10 for r1, r2 in zip(f_i.cpu().numpy(), g_i.cpu().numpy())])
     assert agree >= 0.999
+    check_no_device_error(st)
     st.close()
 
 
@@ -106,4 +108,5 @@ def test_integer_scan_respects_deletes_and_zero_queries():
     gi, gs = st.search(qt, 10, 40, "int16")
     gi = gi.cpu().numpy()
     assert np.all(np.sort(gi[:, :2], axis=1) == keep) and np.all(gi[:, 2:] == -1)
+    check_no_device_error(st)
     st.close()
