@@ -43,6 +43,9 @@ import synth  # noqa: E402
 WORKLOAD = "mlvq4x8-ip-10m-d768"
 METRIC = "LVQ-4x8 distances/s & QPS@recall10 at 10M x 768"
 UNIT = "distances/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one scan_mma launch over
+# 2M rows with the bench's 12,716-query mix (ncu --set full, B300)
+SCAN_MMA_DRAM_BYTES_2M = 1.934105e9 + 0.774121e9
 
 
 def parse():
@@ -469,8 +472,13 @@ def main():
     if scan_kind == "scan_mma":
         achieved = flops_per_launch / per_launch_s / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1400.0
+        # DRAM bytes of one launch: an ncu capture of this kernel at 2M rows
+        # (dram__bytes_read.sum + dram__bytes_write.sum, same query mix),
+        # scaled by the rows (jobs and their code reads grow with the rows)
+        traffic = SCAN_MMA_DRAM_BYTES_2M * n_live / 2e6 if nq == 12716 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu capture at 2M rows scaled by rows" if traffic else None,
                 "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops_sustained; fp16 rate = bf16 rate)"
                 if "bf16_tflops_sustained" in peaks else "fallback"}
     else:
