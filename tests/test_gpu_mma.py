@@ -30,6 +30,8 @@ CASES = [
     (3000, 200, 32, "l2", 4, 8, 16, 20, 40, 10),
     (5000, 96, 32, "l2", 8, 8, 1, 24, 30, 10),
     (3000, 768, 16, "ip", 8, 8, 4, 9, 100, 10),
+    (4000, 768, 32, "ip", 8, 0, 1, 40, 0, 10),     # LVQ-8 single level at d = 768
+    (4000, 768, 32, "l2", 4, 0, 4, 20, 0, 10),     # LVQ-4 single level, M-LVQ
 ]
 
 
@@ -45,15 +47,20 @@ def test_tensor_core_first_level_and_search(case):
     mid = st.export(ids)["mean_id"].cpu().numpy()
     enc = O.encode(x, means, b1, b2, mean_id=mid)
     qt = torch.from_numpy(q).cuda()
-    fi, fs = st.first_level(qt, k1, "fp16")
+    kk = k1 if k1 else k
+    fi, fs = st.first_level(qt, kk, "fp16")
     check_sorted(fs, metric)
     check_scores(q, fi, fs, enc, means, metric, 1, TOL_FP16)
-    check_topk_ids(q, fi, enc, means, metric, k1, TOL_FP16, level=1)
+    check_topk_ids(q, fi, enc, means, metric, kk, TOL_FP16, level=1)
     gi, gs = st.search(qt, k, k1, "fp16")
     check_sorted(gs, metric)
-    # re-rank distances are float32
-    check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-    check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    if b2 and k1:
+        # re-rank distances are float32
+        check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
+        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    else:
+        check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP16)
+        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP16, level=1)
     check_no_device_error(st)
     st.close()
 

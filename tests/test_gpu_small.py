@@ -33,6 +33,8 @@ CASES = [
     (3000, 768, 16, "ip", 8, 8, 4, 1, 100, 10),
     (30000, 200, 16, "l2", 4, 8, 1, 2, 512, 10),
     (100, 96, 4, "l2", 4, 8, 1, 4, 100, 10),
+    (4000, 768, 32, "ip", 8, 0, 1, 2, 0, 10),      # LVQ-8 single level at d = 768
+    (4000, 768, 32, "l2", 4, 0, 4, 3, 0, 10),      # LVQ-4 single level, M-LVQ
 ]
 
 
@@ -48,15 +50,20 @@ def test_integer_first_level_and_search(case):
     mid = st.export(ids)["mean_id"].cpu().numpy()
     enc = O.encode(x, means, b1, b2, mean_id=mid)
     qt = torch.from_numpy(q).cuda()
-    kk = min(k1, n)
-    fi, fs = st.first_level(qt, k1, "int16")
+    k1_ = k1 if k1 else k
+    kk = min(k1_, n)
+    fi, fs = st.first_level(qt, k1_, "int16")
     check_sorted(fs, metric)
     check_scores(q, fi[:, :kk], fs[:, :kk], enc, means, metric, 1, TOL_FP16)
     check_topk_ids(q, fi[:, :kk], enc, means, metric, kk, TOL_FP16, level=1)
     gi, gs = st.search(qt, k, k1, "int16")
     check_sorted(gs, metric)
-    check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-    check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    if b2 and k1:
+        check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
+        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+    else:
+        check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP16)
+        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP16, level=1)
     check_no_device_error(st)
     st.close()
 
