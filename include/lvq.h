@@ -150,6 +150,20 @@ lvq_status lvq_publish(lvq_store *store, const int64_t *ids, int64_t n, lvq_stre
 lvq_status lvq_delete(lvq_store *store, const int64_t *ids, int64_t n, int64_t *out_n_deleted,
                       lvq_stream_t stream);
 
+/* M-LVQ centre update (Sec. 3.2, multi-means LVQ; re-encoding a centre's
+ * vectors after an update is what makes M-LVQ suited to streaming data):
+ * replace centre m by new_mean and re-encode every live slot tagged with m
+ * against it, from the slot's float32 two-level reconstruction
+ *   y = fl(fl(D c) + l) [+ fl(fl(D2 c2) + l2)],  x = fl(mu_m + y),
+ * with the same per-vector encoding as lvq_insert; the tag stays m.  Other
+ * slots are untouched.
+ * new_mean: d float32 (device).  out_count: host int64, receives the number
+ * of slots re-encoded.  Synchronises the stream once (to size the work);
+ * no search or update of this store may run concurrently.  m outside
+ * [0, n_means) returns LVQ_EINVAL. */
+lvq_status lvq_update_mean(lvq_store *store, int32_t m, const float *new_mean, int64_t *out_count,
+                           lvq_stream_t stream);
+
 /* Exhaustive search over all live slots (Sec. 3.2 scoring, App. C re-rank).
  * q: nq x d float32 queries.
  * k1: first-level candidates per query, 1 .. 512; 0 (or a store without a

@@ -40,6 +40,7 @@ __all__ = [
     "decode_second", "decode", "score", "best_first", "topk", "search_exhaustive",
     "search_candidates", "rerank", "ground_truth", "recall_at_k", "eps_first", "eps_second",
     "SlotReplay", "StoreFull", "pad_value", "take", "first_level_candidates",
+    "reconstruct_f32", "update_mean",
 ]
 
 
@@ -348,6 +349,46 @@ def recall_at_k(found: np.ndarray, truth: np.ndarray, k: int) -> float:
     for s, g in zip(found, truth):
         hits += len(set(s[s >= 0].tolist()) & set(g[g >= 0].tolist()))
     return hits / (k * len(found))
+
+
+# --------------------------------------------------------------------------
+# M-LVQ centre update (Sec. 3.2): re-encoding a centre's vectors
+# --------------------------------------------------------------------------
+
+def reconstruct_f32(enc: dict, means) -> np.ndarray:
+    """The stored records decoded in float32, each operation rounded:
+    y = D*c + l, plus (second level) D2*c2 + l2, then x = mu_m + y.  This is
+    the input of a re-encode, so its rounding is fixed step by step."""
+    d = enc["codes1"].shape[1]
+    means = np.asarray(means, dtype=F32).reshape(-1, d)
+    step = enc["step"].astype(F32)[:, None]
+    y = ((step * enc["codes1"].astype(F32)).astype(F32) + enc["lower"].astype(F32)[:, None]).astype(F32)
+    if enc.get("bits2"):
+        lower2, step2 = residual_grid(enc["step"], enc["bits2"])
+        r = ((step2[:, None] * enc["codes2"].astype(F32)).astype(F32) + lower2[:, None]).astype(F32)
+        y = (y + r).astype(F32)
+    return (means[enc["mean_id"].astype(np.int64)] + y).astype(F32)
+
+
+def update_mean(enc: dict, means, m: int, new_mean, live=None):
+    """Replace centre m by new_mean and re-encode every live record tagged
+    with m against it, from its float32 reconstruction; tags stay m and the
+    other records are untouched.  Returns (new enc, new means, count)."""
+    d = enc["codes1"].shape[1]
+    n = len(enc["lower"])
+    live = np.ones(n, dtype=bool) if live is None else np.asarray(live, dtype=bool)
+    rows = np.nonzero(live & (enc["mean_id"] == m))[0]
+    means2 = np.array(np.asarray(means, dtype=F32).reshape(-1, d), copy=True)
+    x = reconstruct_f32(take(enc, rows), means2)
+    means2[m] = np.asarray(new_mean, dtype=F32)
+    e = encode(x, means2, enc["bits1"], enc.get("bits2") or 0, mean_id=np.full(len(rows), m, dtype=np.uint8))
+    out = dict(enc)
+    for key in ("codes1", "codes2", "lower", "step"):
+        if enc.get(key) is not None:
+            arr = np.array(enc[key], copy=True)
+            arr[rows] = e[key]
+            out[key] = arr
+    return out, means2, len(rows)
 
 
 # --------------------------------------------------------------------------

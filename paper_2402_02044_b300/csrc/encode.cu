@@ -60,9 +60,9 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
         xv[i][e] = (g < groups && j < d) ? __ldg(xr + j) : 0.0f;
       }
     }
-    // Def. 1: nearest centre, lowest index on ties.
-    int m_star = 0;
-    if (st.n_means > 1) {
+    // Def. 1: nearest centre, lowest index on ties (or the forced one).
+    int m_star = out.force_mean >= 0 ? out.force_mean : 0;
+    if (st.n_means > 1 && out.force_mean < 0) {
       float best = __int_as_float(0x7f800000);
       for (int m = 0; m < st.n_means; ++m) {
         const float* mu = st.means + (int64_t)m * d;
@@ -391,6 +391,73 @@ cudaError_t launch_encode(const DeviceStore& st, const float* x, int64_t n, cons
     default:
       encode_kernel<16><<<blocks, threads, 0, stream>>>(st, x, n, out); break;
   }
+  return cudaGetLastError();
+}
+
+// ---- M-LVQ local re-encode ------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(256) select_mean_kernel(DeviceStore st, int64_t n_rows, int m, int64_t* list,
+                                                          unsigned long long* count) {
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: every lane takes part in each ballot
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_rows;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = base + lane;
+    const bool take = s < n_rows && is_live(st.live, s) && st.mean_id[s] == m;
+    const unsigned bal = __ballot_sync(FULL, take);
+    if (!bal) continue;
+    unsigned long long at = 0;
+    if (lane == __ffs(bal) - 1) at = atomicAdd(count, (unsigned long long)__popc(bal));
+    at = __shfl_sync(FULL, at, __ffs(bal) - 1);
+    if (take) list[at + __popc(bal & ((1u << lane) - 1u))] = s;
+  }
+}
+
+// The stored record decoded in float32, each operation rounded:
+//   y = fl(fl(D c) + l); with a second level y = fl(y + fl(fl(D2 c2) + l2));
+//   x = fl(mu + y).  One warp per slot.
+__global__ void __launch_bounds__(256) reconstruct_kernel(DeviceStore st, const int64_t* __restrict__ list,
+                                                          int64_t n, const float* __restrict__ mu,
+                                                          float* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int64_t s = list[i];
+  const float lo = st.lower[s], step = st.step[s];
+  const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+  const uint8_t* r1 = st.codes1 + s * st.row1;
+  const uint8_t* r2 = st.bits2 ? st.codes2 + s * st.row2 : nullptr;
+  for (int j = lane; j < st.d; j += 32) {
+    uint32_t c;
+    if (st.bits1 == 4) {
+      // word j/8 holds dim 8w+2p at bits 4p and dim 8w+2p+1 at bits 16+4p
+      const uint32_t w = reinterpret_cast<const uint32_t*>(r1)[j >> 3];
+      const int e = j & 7;
+      c = (w >> ((e & 1) ? 16 + 4 * (e >> 1) : 4 * (e >> 1))) & 0xFu;
+    } else {
+      c = r1[j];
+    }
+    float y = __fadd_rn(__fmul_rn(step, (float)c), lo);
+    if (r2) y = __fadd_rn(y, __fadd_rn(__fmul_rn(step2, (float)r2[j]), lo2));
+    x[i * st.d + j] = __fadd_rn(mu[j], y);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_select_mean(const DeviceStore& st, int64_t n_rows, int m, int64_t* list,
+                               unsigned long long* count, cudaStream_t stream) {
+  if (n_rows <= 0) return cudaSuccess;
+  const int64_t b = ceil_div(n_rows, 256);
+  select_mean_kernel<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, stream>>>(st, n_rows, m, list, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(const DeviceStore& st, const int64_t* list, int64_t n, const float* mu, float* x,
+                               cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  reconstruct_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, stream>>>(st, list, n, mu, x);
   return cudaGetLastError();
 }
 

@@ -17,11 +17,19 @@ struct EncodeOut {
   // store layout (lvq_insert): vector i goes to slot slots[i]
   const int64_t* slots = nullptr;
   const int32_t* abort_flag = nullptr;  // set when the insert was abandoned
+  int force_mean = -1;                  // >= 0: every vector takes this centre (no assignment)
 };
 
 cudaError_t launch_encode(const DeviceStore& st, const float* x, int64_t n, const EncodeOut& out,
                           cudaStream_t stream);
 size_t alloc_scratch_bytes(int64_t capacity);
+// M-LVQ local re-encode: the live slots below n_rows tagged with mean m go to
+// list[0 .. *count) (count: one int64 that must start at zero)
+cudaError_t launch_select_mean(const DeviceStore& st, int64_t n_rows, int m, int64_t* list,
+                               unsigned long long* count, cudaStream_t stream);
+// float32 reconstruction of slots list[0..n) with centre mu (d floats): x[i]
+cudaError_t launch_reconstruct(const DeviceStore& st, const int64_t* list, int64_t n, const float* mu, float* x,
+                               cudaStream_t stream);
 cudaError_t launch_alloc_slots(const DeviceStore& st, int64_t n, int64_t* out_ids, int32_t* scratch,
                                int32_t* abort_flag, cudaStream_t stream);
 cudaError_t launch_publish(const DeviceStore& st, const int64_t* ids, int64_t n, const int32_t* abort_flag,

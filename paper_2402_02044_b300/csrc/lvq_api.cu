@@ -13,6 +13,7 @@ using namespace lvq;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int64_t kReencodeChunk = 65536;  // rows reconstructed and re-encoded per pass
 
 // counters block layout (device, int64 words)
 enum { kCtrLive = 0, kCtrAbort = 1, kCtrDelCount = 2, kCtrWords = 4 };
@@ -459,6 +460,49 @@ lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_
            launch_delete(s->ds, ids, n, out_n_deleted, reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount),
                          ctr + kCtrLive, (cudaStream_t)stream),
            "delete");
+  return LVQ_OK;
+}
+
+lvq_status lvq_update_mean(lvq_store* s, int32_t m, const float* new_mean, int64_t* out_count, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (!new_mean || !out_count) return fail(s, LVQ_EINVAL, "null pointer");
+  if (m < 0 || m >= s->ds.n_means) return fail(s, LVQ_EINVAL, "mean index out of range");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  const DeviceStore& st = s->ds;
+  const cudaStream_t str = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(s->mu);
+  const int64_t n_rows = root_of(s)->rows_bound.load();
+  const int64_t chunk = n_rows < kReencodeChunk ? (n_rows > 0 ? n_rows : 1) : kReencodeChunk;
+  Carver sizer(nullptr);
+  sizer.take<int64_t>((size_t)(n_rows > 0 ? n_rows : 1));
+  sizer.take<unsigned long long>(1);
+  sizer.take<float>((size_t)st.d);
+  sizer.take<float>((size_t)chunk * st.d);
+  lvq_status rc = ensure_ws(s, sizer.off);
+  if (rc != LVQ_OK) return rc;
+  Carver c(s->ws);
+  int64_t* list = c.take<int64_t>((size_t)(n_rows > 0 ? n_rows : 1));
+  unsigned long long* cnt = c.take<unsigned long long>(1);
+  float* old_mu = c.take<float>((size_t)st.d);
+  float* xbuf = c.take<float>((size_t)chunk * st.d);
+  float* mu_m = st.means + (int64_t)m * st.d;
+  // the old centre is kept for the reconstructions, then replaced
+  LVQ_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(*cnt), str), "memset");
+  LVQ_CUDA(s, cudaMemcpyAsync(old_mu, mu_m, (size_t)st.d * 4, cudaMemcpyDeviceToDevice, str), "copy centre");
+  LVQ_CUDA(s, launch_select_mean(st, n_rows, m, list, cnt, str), "select_mean");
+  LVQ_CUDA(s, cudaMemcpyAsync(mu_m, new_mean, (size_t)st.d * 4, cudaMemcpyDeviceToDevice, str), "copy centre");
+  unsigned long long count = 0;
+  LVQ_CUDA(s, cudaMemcpyAsync(&count, cnt, sizeof(count), cudaMemcpyDeviceToHost, str), "copy count");
+  LVQ_CUDA(s, cudaStreamSynchronize(str), "synchronize");
+  for (int64_t off = 0; off < (int64_t)count; off += chunk) {
+    const int64_t nb = (int64_t)count - off < chunk ? (int64_t)count - off : chunk;
+    LVQ_CUDA(s, launch_reconstruct(st, list + off, nb, old_mu, xbuf, str), "reconstruct");
+    EncodeOut out;
+    out.slots = list + off;
+    out.force_mean = m;
+    LVQ_CUDA(s, launch_encode(st, xbuf, nb, out, str), "encode");
+  }
+  *out_count = (int64_t)count;
   return LVQ_OK;
 }
 

@@ -60,6 +60,7 @@ _SIGS = {
     "lvq_delete": [_P, _P, _I64, _P, _P],
     "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
+    "lvq_update_mean": [_P, _I32, _P, ctypes.POINTER(_I64), _P],
     "lvq_search_exhaustive_static": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
     "lvq_search_candidates": [_P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P],
     "lvq_rerank": [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P],
@@ -186,6 +187,13 @@ def lvq_search_exhaustive_static(store, q, k1, k, out_ids, out_scores, stream=No
                                                _ptr(out_ids, torch.int64, "out_ids"),
                                                _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
            "lvq_search_exhaustive_static")
+
+
+def lvq_update_mean(store, m, new_mean, stream=None) -> int:
+    n = _I64(0)
+    _check(load().lvq_update_mean(store, m, _ptr(new_mean, torch.float32, "new_mean"), ctypes.byref(n),
+                                  _stream(stream)), "lvq_update_mean")
+    return int(n.value)
 
 
 def lvq_search_first_level(store, q, k1, precision, out_ids, out_scores, stream=None):
@@ -324,6 +332,10 @@ class Store:
         sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
         lvq_search_exhaustive(self.handle, q, k1, k, precision, ids, sc, stream)
         return ids, sc
+
+    def update_mean(self, m: int, new_mean: torch.Tensor, stream=None) -> int:
+        """Replace centre m and re-encode its live vectors; returns their number."""
+        return lvq_update_mean(self.handle, m, new_mean.contiguous(), stream)
 
     def first_level(self, q: torch.Tensor, k1: int, precision="fp32", stream=None):
         ids = torch.empty((q.shape[0], k1), dtype=torch.int64, device=q.device)

@@ -311,3 +311,68 @@ def test_planted_mistakes_are_caught(monkeypatch):
     fact = q @ mu.astype(np.float64)[0][:, None] + enc["lower"][None] * q.sum(1)[:, None] \
         + enc["step"][None] * (q @ enc["codes1"].T.astype(np.float64))
     assert np.allclose(q @ good.T, fact) and not np.allclose(q @ bad.T, fact)
+
+
+# ---- M-LVQ centre update (Sec. 3.2) -------------------------------------------
+
+def _on_grid_store():
+    """Two integer centres and rows x = mu_m + l + c with integer l and codes
+    c in [0, 15] (0 and 15 present in each row): every float32 step is exact."""
+    g = np.random.default_rng(11)
+    d, n = 12, 40
+    means = g.integers(-20, 20, (2, d)).astype(F32)
+    m = np.arange(n) % 2
+    lower = g.integers(-9, 9, n).astype(F32)
+    c = g.integers(0, 16, (n, d))
+    c[:, 0], c[:, 1] = 0, 15
+    x = (means[m] + lower[:, None] + c).astype(F32)
+    return x, means, m.astype(np.uint8), c
+
+
+def test_update_mean_by_a_constant_shift_is_exact():
+    x, means, m, c = _on_grid_store()
+    enc = O.encode(x, means, 4, mean_id=m)
+    assert np.array_equal(enc["codes1"], c) and np.all(enc["step"] == 1)
+    shifted = means[1] + F32(3)
+    new, means2, cnt = O.update_mean(enc, means, 1, shifted)
+    t = m == 1
+    assert cnt == t.sum()
+    # codes and steps kept, lower bounds down by 3, the same vectors decoded
+    assert np.array_equal(new["codes1"], enc["codes1"]) and np.array_equal(new["step"], enc["step"])
+    assert np.array_equal(new["lower"][t], enc["lower"][t] - 3) and np.array_equal(new["lower"][~t], enc["lower"][~t])
+    assert np.array_equal(O.decode_first(new, means2), O.decode_first(enc, means))
+    # a mistaken update that reconstructs with the new centre decodes elsewhere
+    wrong = O.encode(O.reconstruct_f32(enc, means2), means2, 4, mean_id=m)
+    assert not np.array_equal(O.decode_first(wrong, means2)[t], O.decode_first(enc, means)[t])
+
+
+def test_reconstruct_f32_is_the_float64_decode_up_to_rounding():
+    mix = synth.Mixture(d=40, n_comp=4, sigma=0.3, seed=5)
+    x = mix.base(300, threads=1)
+    means = synth.kmeans_means(x, 3, seed=5, iters=5)
+    enc = O.encode(x, means, 4, 8)
+    r = O.reconstruct_f32(enc, means).astype(np.float64)
+    ref = O.decode_second(enc, means)
+    assert np.all(np.abs(r - ref) <= 4 * np.finfo(np.float32).eps * (np.abs(ref) + 1))
+
+
+def test_update_mean_re_encodes_only_live_tagged_rows_within_the_bound():
+    mix = synth.Mixture(d=40, n_comp=4, sigma=0.3, seed=6)
+    x = mix.base(400, threads=1)
+    means = synth.kmeans_means(x, 3, seed=6, iters=5)
+    enc = O.encode(x, means, 4, 8)
+    live = np.ones(400, bool)
+    live[::7] = False
+    m = int(np.bincount(enc["mean_id"]).argmax())
+    new_mu = means[m] + F32(0.05) * np.sin(np.arange(40, dtype=F32))
+    before = O.reconstruct_f32(enc, means)
+    new, means2, cnt = O.update_mean(enc, means, m, new_mu, live=live)
+    t = live & (enc["mean_id"] == m)
+    assert cnt == t.sum() > 0 and np.array_equal(new["mean_id"], enc["mean_id"])
+    for key in ("codes1", "codes2", "lower", "step"):
+        assert np.array_equal(new[key][~t], enc[key][~t])
+    # the re-encoded two-level decode is within half a residual step of the
+    # reconstruction it was encoded from (plus float rounding)
+    _, step2 = O.residual_grid(new["step"][t], 8)
+    err = np.abs(O.decode_second(O.take(new, np.nonzero(t)[0]), means2) - before[t])
+    assert np.all(err <= step2[:, None] / 2 * (1 + 1e-4) + 1e-6)
