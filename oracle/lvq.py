@@ -40,7 +40,7 @@ __all__ = [
     "decode_second", "decode", "score", "best_first", "topk", "search_exhaustive",
     "search_candidates", "rerank", "ground_truth", "recall_at_k", "eps_first", "eps_second",
     "SlotReplay", "StoreFull", "pad_value", "take", "first_level_candidates",
-    "reconstruct_f32", "update_mean",
+    "reconstruct_f32", "update_mean", "beam_search",
 ]
 
 
@@ -389,6 +389,57 @@ def update_mean(enc: dict, means, m: int, new_mean, live=None):
             arr[rows] = e[key]
             out[key] = arr
     return out, means2, len(rows)
+
+
+# --------------------------------------------------------------------------
+# Greedy beam search over a graph (Alg. 1), first-level scores
+# --------------------------------------------------------------------------
+
+def beam_search(enc: dict, means, q, graph, starts, L: int, k: int, metric: str, live=None, max_expand=None):
+    """Alg. 1 for each query: a search list of at most L nodes ordered by
+    (first-level score, id), seeded with ``starts``; repeatedly expand the
+    best node not yet expanded (score its out-neighbours not seen before and
+    keep the L best of the list) until every listed node is expanded or
+    ``max_expand`` expansions were made.  Deleted nodes are never listed.
+    Returns the k best listed (ids int64 [nq, k], scores float64 [nq, k],
+    padded with -1 / pad_value)."""
+    q = np.atleast_2d(np.asarray(q, dtype=F32))
+    graph = np.asarray(graph)
+    n = len(enc["lower"])
+    live = np.ones(n, dtype=bool) if live is None else np.asarray(live, dtype=bool)
+    xh = decode_first(enc, means)
+    out_ids = np.full((len(q), k), -1, dtype=np.int64)
+    out_s = np.full((len(q), k), pad_value(metric), dtype=F64)
+    key = (lambda s: s) if metric == L2 else (lambda s: -s)
+    for i in range(len(q)):
+        sc = score(q[i], xh, metric)[0]
+        seen = set()
+        lst = []                      # (key, id)
+        for s in starts:
+            s = int(s)
+            if 0 <= s < n and live[s] and s not in seen:
+                seen.add(s)
+                lst.append((key(sc[s]), s))
+        lst = sorted(lst)[:L]
+        expanded = set()
+        steps = 0
+        while max_expand is None or steps < max_expand:
+            nxt = next((v for v in lst if v[1] not in expanded), None)
+            if nxt is None:
+                break
+            expanded.add(nxt[1])
+            steps += 1
+            for u in graph[nxt[1]]:
+                u = int(u)
+                if u < 0 or u >= n or u in seen or not live[u]:
+                    continue
+                seen.add(u)
+                lst.append((key(sc[u]), u))
+            lst = sorted(lst)[:L]
+        top = lst[:k]
+        out_ids[i, :len(top)] = [u for _, u in top]
+        out_s[i, :len(top)] = [sc[u] for _, u in top]
+    return out_ids, out_s
 
 
 # --------------------------------------------------------------------------

@@ -376,3 +376,35 @@ def test_update_mean_re_encodes_only_live_tagged_rows_within_the_bound():
     _, step2 = O.residual_grid(new["step"][t], 8)
     err = np.abs(O.decode_second(O.take(new, np.nonzero(t)[0]), means2) - before[t])
     assert np.all(err <= step2[:, None] / 2 * (1 + 1e-4) + 1e-6)
+
+
+# ---- greedy beam search (Alg. 1) ---------------------------------------------
+
+def test_beam_search_on_a_complete_graph_is_the_exhaustive_search():
+    mix = synth.Mixture(d=16, n_comp=4, sigma=0.3, seed=8)
+    x = mix.base(60, threads=1)
+    means = synth.sample_mean(x)[None]
+    enc = O.encode(x, means, 4)
+    q = mix.queries(3, threads=1)
+    graph = np.array([[j for j in range(60) if j != i] for i in range(60)])
+    live = np.ones(60, bool)
+    live[[3, 17]] = False
+    for metric in ("l2", "ip"):
+        bi, bs = O.beam_search(enc, means, q, graph, [0], L=60, k=10, metric=metric, live=live)
+        ei, es = O.search_exhaustive(enc, means, q, 0, 10, metric, live=live)
+        assert np.array_equal(bi, ei) and np.allclose(bs, es)
+
+
+def test_beam_search_follows_the_graph():
+    # a path 0 - 1 - ... - 9 in one dimension, query beyond node 9: from node
+    # 0 with L = 2 the search walks the path and ends at the far end; with no
+    # expansions it returns the start
+    x = np.arange(10, dtype=F32)[:, None] * np.ones((1, 8), F32)
+    means = np.zeros((1, 8), F32)
+    enc = O.encode(x, means, 8)
+    q = np.full((1, 8), 20.0, F32)
+    graph = np.array([[max(i - 1, 0), min(i + 1, 9)] for i in range(10)])
+    ids, _ = O.beam_search(enc, means, q, graph, [0], L=2, k=2, metric="l2")
+    assert ids[0].tolist() == [9, 8]
+    ids, _ = O.beam_search(enc, means, q, graph, [0], L=2, k=2, metric="l2", max_expand=0)
+    assert ids[0].tolist() == [0, -1]
