@@ -164,6 +164,23 @@ lvq_status lvq_delete(lvq_store *store, const int64_t *ids, int64_t n, int64_t *
 lvq_status lvq_update_mean(lvq_store *store, int32_t m, const float *new_mean, int64_t *out_count,
                            lvq_stream_t stream);
 
+/* Greedy beam search over a caller-given graph (Alg. 1): per query a
+ * search list of at most L nodes ordered by first-level score, seeded with
+ * the start nodes; the best node not yet expanded is expanded (its live,
+ * unseen out-neighbours are scored with the first level in float32) until
+ * every listed node is expanded or max_expand expansions were made; the k1
+ * best listed nodes are then re-ranked with both levels to k (k1 = 0 or a
+ * store without a second level: the k best by first level).
+ * graph: n_graph x R int32 out-neighbour ids (device; -1 = no edge; ids
+ *   >= n_graph or deleted are skipped).  starts: n_starts int64 (device),
+ *   1 <= n_starts <= L.  L: 1 .. 1024, >= k and k1.  max_expand: 0 = 4 L.
+ * Outputs as in lvq_search_exhaustive.  LVQ_EINVAL when the seen-set of
+ * (n_starts + R max_expand) ids does not fit in shared memory. */
+lvq_status lvq_search_graph(const lvq_store *store, const float *q, int64_t nq, const int32_t *graph,
+                            int64_t n_graph, int32_t R, const int64_t *starts, int32_t n_starts, int32_t L,
+                            int32_t max_expand, int32_t k1, int32_t k, int64_t *out_ids, float *out_scores,
+                            lvq_stream_t stream);
+
 /* Exhaustive search over all live slots (Sec. 3.2 scoring, App. C re-rank).
  * q: nq x d float32 queries.
  * k1: first-level candidates per query, 1 .. 512; 0 (or a store without a

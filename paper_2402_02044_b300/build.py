@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblvq.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lvq_api.cu", "encode.cu", "select.cu", "scan_fp32.cu", "scan_mma.cu", "scan_small.cu"]
+SOURCES = ["lvq_api.cu", "encode.cu", "select.cu", "scan_fp32.cu", "scan_mma.cu", "scan_small.cu", "graph.cu"]
 HEADERS = ["lvq_internal.cuh", "kernels.cuh", "topk.cuh", "score.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -104,6 +104,18 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
 // persistent CTAs of the small-batch scan: one per SM, at most one per tile
 int small_grid(int64_t n_rows, int sm_count);
 
+// ---- greedy beam search over a graph (graph.cu) --------------------------------
+// slots of the seen-set (power of two, at most half full) and shared memory
+int beam_set_slots(int n_starts, int R, int max_expand);
+size_t beam_smem(const DeviceStore& st, int L, int R, int H);
+// first-level keys of the k1 best listed nodes per query into keys[nq][k1]
+// (kNoKey pads) and their ids into ids[nq][k1] (-1 pads)
+cudaError_t launch_beam(const DeviceStore& st, const float* q, int64_t nq, const int32_t* graph, int64_t n_graph,
+                        int R, const int64_t* starts, int n_starts, int L, int max_expand, int k1, uint64_t* keys,
+                        int64_t* ids, cudaStream_t stream);
+cudaError_t launch_keys_to_results(const uint64_t* keys, int64_t nq, int k1, int k, int metric, int64_t* out_ids,
+                                  float* out_scores, cudaStream_t stream);
+
 // ---- selection and re-ranking ----------------------------------------------
 // Merge the per-split lists of each query into its k1 best, then either write
 // the k best (first level) or re-rank the k1 with both levels and write k.

@@ -506,6 +506,50 @@ lvq_status lvq_update_mean(lvq_store* s, int32_t m, const float* new_mean, int64
   return LVQ_OK;
 }
 
+lvq_status lvq_search_graph(const lvq_store* cs, const float* q, int64_t nq, const int32_t* graph, int64_t n_graph,
+                            int32_t R, const int64_t* starts, int32_t n_starts, int32_t L, int32_t max_expand,
+                            int32_t k1, int32_t k, int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  lvq_status rc = check_q(cs, q, nq);
+  if (rc != LVQ_OK) return rc;
+  lvq_store* s = const_cast<lvq_store*>(cs);
+  const DeviceStore& st = s->ds;
+  if (k < 1 || k > kMaxK1) return fail(s, LVQ_EINVAL, "k out of range");
+  if (k1 < 0 || k1 > kMaxK1 || (k1 > 0 && k1 < k)) return fail(s, LVQ_EINVAL, "k1 out of range");
+  if (R < 1 || R > 256 || n_graph < 1 || n_graph > st.capacity) return fail(s, LVQ_EINVAL, "graph shape out of range");
+  if (L < 1 || L > 1024 || L < k || L < k1) return fail(s, LVQ_EINVAL, "L must be at least k and k1 (and at most 1024)");
+  if (n_starts < 1 || n_starts > L) return fail(s, LVQ_EINVAL, "n_starts out of range (1 .. L)");
+  if (max_expand < 0) return fail(s, LVQ_EINVAL, "max_expand < 0");
+  if (nq > 0 && (!graph || !starts || !out_ids || !out_scores)) return fail(s, LVQ_EINVAL, "null pointer");
+  if (nq == 0) return LVQ_OK;
+  const int expand = max_expand > 0 ? max_expand : 4 * L;
+  if (beam_smem(st, L, R, beam_set_slots(n_starts, R, expand)) > 220 * 1024)
+    return fail(s, LVQ_EINVAL, "the seen-set of L, R and max_expand does not fit in shared memory");
+  const bool two = st.bits2 && k1 > 0;
+  const int kk1 = two ? k1 : k;
+  std::lock_guard<std::mutex> g(s->mu);
+  Carver sizer(nullptr);
+  sizer.take<uint64_t>((size_t)nq * kk1);
+  sizer.take<int64_t>((size_t)nq * kk1);
+  rc = ensure_ws(s, sizer.off);
+  if (rc != LVQ_OK) return rc;
+  Carver c(s->ws);
+  uint64_t* keys = c.take<uint64_t>((size_t)nq * kk1);
+  int64_t* ids = c.take<int64_t>((size_t)nq * kk1);
+  const cudaStream_t str = (cudaStream_t)stream;
+  {
+    Prof p(s, str, LVQ_K_GATHER, 2);
+    LVQ_CUDA(s, launch_beam(st, q, nq, graph, n_graph, R, starts, n_starts, L, expand, kk1, keys, ids, str), "beam");
+  }
+  if (two) {
+    QueryPrep none{};
+    Prof p(s, str, LVQ_K_RERANK);
+    LVQ_CUDA(s, launch_rerank(st, q, nq, none, ids, kk1, k, out_ids, out_scores, str), "rerank");
+  } else {
+    LVQ_CUDA(s, launch_keys_to_results(keys, nq, kk1, k, st.metric, out_ids, out_scores, str), "results");
+  }
+  return LVQ_OK;
+}
+
 lvq_status lvq_search_exhaustive(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t k,
                                  int32_t precision, int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
   lvq_status rc = check_q(cs, q, nq);

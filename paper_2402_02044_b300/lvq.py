@@ -61,6 +61,7 @@ _SIGS = {
     "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
     "lvq_update_mean": [_P, _I32, _P, ctypes.POINTER(_I64), _P],
+    "lvq_search_graph": [_P, _P, _I64, _P, _I64, _I32, _P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_exhaustive_static": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
     "lvq_search_candidates": [_P, _P, _I64, _P, _I32, _I32, _I32, _P, _P, _P],
     "lvq_rerank": [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P],
@@ -194,6 +195,14 @@ def lvq_update_mean(store, m, new_mean, stream=None) -> int:
     _check(load().lvq_update_mean(store, m, _ptr(new_mean, torch.float32, "new_mean"), ctypes.byref(n),
                                   _stream(stream)), "lvq_update_mean")
     return int(n.value)
+
+
+def lvq_search_graph(store, q, graph, starts, L, max_expand, k1, k, out_ids, out_scores, stream=None):
+    _check(load().lvq_search_graph(store, _ptr(q, torch.float32, "q"), q.shape[0], _ptr(graph, torch.int32, "graph"),
+                                   graph.shape[0], graph.shape[1], _ptr(starts, torch.int64, "starts"),
+                                   starts.numel(), L, max_expand, k1, k, _ptr(out_ids, torch.int64, "out_ids"),
+                                   _ptr(out_scores, torch.float32, "out_scores"), _stream(stream)),
+           "lvq_search_graph")
 
 
 def lvq_search_first_level(store, q, k1, precision, out_ids, out_scores, stream=None):
@@ -331,6 +340,14 @@ class Store:
         ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)
         sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
         lvq_search_exhaustive(self.handle, q, k1, k, precision, ids, sc, stream)
+        return ids, sc
+
+    def search_graph(self, q: torch.Tensor, graph: torch.Tensor, starts: torch.Tensor, k: int, k1: int = 0,
+                     L: int = 64, max_expand: int = 0, stream=None):
+        ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)
+        sc = torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device)
+        lvq_search_graph(self.handle, q, graph.contiguous(), starts.contiguous(), L, max_expand, k1, k, ids, sc,
+                         stream)
         return ids, sc
 
     def update_mean(self, m: int, new_mean: torch.Tensor, stream=None) -> int:
