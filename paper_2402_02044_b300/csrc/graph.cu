@@ -188,7 +188,8 @@ cudaError_t launch_beam(const DeviceStore& st, const float* q, int64_t nq, const
   const size_t sm = beam_smem(st, L, R, H);
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // the kernel also has a few bytes of static shared memory
+    const cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
