@@ -32,6 +32,9 @@ CASES = [
     (3000, 768, 16, "ip", 8, 8, 4, 9, 100, 10),
     (4000, 768, 32, "ip", 8, 0, 1, 40, 0, 10),     # LVQ-8 single level at d = 768
     (4000, 768, 32, "l2", 4, 0, 4, 20, 0, 10),     # LVQ-4 single level, M-LVQ
+    (2000, 4096, 8, "ip", 4, 8, 1, 20, 64, 10),    # the largest d (narrow query tiles)
+    (3000, 64, 16, "l2", 4, 8, 256, 40, 40, 10),   # the most centres
+    (6000, 128, 16, "ip", 4, 8, 1, 50, 512, 10),   # the largest k1
 ]
 
 

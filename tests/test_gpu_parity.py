@@ -89,6 +89,7 @@ SEARCH_CASES = [
     (3000, 200, 32, "l2", 4, 8, 16, 20, 40, 10),    # M-LVQ L2
     (5000, 768, 64, "ip", 4, 8, 16, 17, 100, 10),   # M-LVQ IP
     (1500, 13, 4, "ip", 8, 8, 1, 5, 30, 30),
+    (1500, 4096, 8, "ip", 4, 8, 1, 5, 32, 10),      # the largest d
 ]
 
 

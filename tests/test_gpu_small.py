@@ -35,6 +35,8 @@ CASES = [
     (100, 96, 4, "l2", 4, 8, 1, 4, 100, 10),
     (4000, 768, 32, "ip", 8, 0, 1, 2, 0, 10),      # LVQ-8 single level at d = 768
     (4000, 768, 32, "l2", 4, 0, 4, 3, 0, 10),      # LVQ-4 single level, M-LVQ
+    (2000, 4096, 8, "l2", 4, 8, 1, 2, 64, 10),     # the largest d
+    (3000, 64, 16, "ip", 4, 8, 256, 4, 40, 10),    # the most centres
 ]
 
 
