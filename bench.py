@@ -487,6 +487,13 @@ def main():
         peak = 148 * 128 * 2 * mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flops x clock
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x median SM clock"}
+    # the ID-gather kernel of the step (candidate ids, codes and per-row
+    # constants of every candidate, re-rank reads not counted)
+    g_ms = prof["gather"][0] / max(prof["gather"][1], 1)
+    g_bytes = nq_g * C * (384 + 4 + 4 + 1 + 8)
+    gather_roof = {"kernel": "gather_kernel", "kernel_ms": g_ms, "algorithmic_bytes_per_launch": g_bytes,
+                   "hbm_gbs": g_bytes / g_ms / 1e6 if g_ms else None, "peak_gbs": peaks.get("hbm_gbs"),
+                   "frac": g_bytes / g_ms / 1e6 / peaks["hbm_gbs"] if g_ms and peaks.get("hbm_gbs") else None}
     roof["kernel"] = scan_kind
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["hbm_gbs_equiv"] = bytes_per_launch / per_launch_s / 1e9
@@ -502,7 +509,7 @@ def main():
                        "k1": 100, "k": 10, "gather_queries": nq_g, "gather_candidates": C,
                        "updates_per_step": B_upd, "l2_flush": "not needed: 3.9 GB of codes > 126 MB L2",
                        "precision": precision},
-            "qps": qps, "recall_at_10": None, "small_batch": small, "serve": serve,
+            "qps": qps, "recall_at_10": None, "small_batch": small, "serve": serve, "gather_roofline": gather_roof,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
             "setup_s": t_setup}

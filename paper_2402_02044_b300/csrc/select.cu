@@ -228,47 +228,54 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
   const float qs = ip ? p.qsum[qi] : 0.0f;
   const float* cmq = ip ? p.cm + (int64_t)qi * st.n_means : nullptr;
   const int64_t* cl = cand + (int64_t)qi * n_cand;
+  // S lanes score one candidate (its code words spread over the lanes, so a
+  // row is read with a few wide loads); a warp scores 32 / S at a time
+  const int S = groups >= 32 ? 32 : pow2_at_least(groups);
+  const int per_warp = 32 / S;
+  const int lane = threadIdx.x & 31, sub = lane / S, sl = lane % S;
+  const int slot0 = (threadIdx.x >> 5) * per_warp + sub;
+  const int nsub = (kGatherThreads / 32) * per_warp;
   for (int base = 0; base < n_cand; base += kGatherThreads) {
-    const int i = base + threadIdx.x;
-    if (i < n_cand) {
-      const int64_t s = cl[i];
-      if (s >= 0 && s < st.capacity && is_live(st.live, s)) {
+    for (int j0 = 0; j0 < kGatherThreads; j0 += nsub) {
+      const int i = base + j0 + slot0;
+      const int64_t s = i < n_cand ? cl[i] : -1;
+      const bool ok = s >= 0 && s < st.capacity && is_live(st.live, s);
+      float acc = 0.0f, lo = 0.0f, step = 0.0f;
+      int m = 0;
+      if (ok) {
         const uint8_t* row = st.codes1 + s * st.row1;
-        const float lo = __ldg(st.lower + s), step = __ldg(st.step + s);
-        const int m = __ldg(st.mean_id + s);
-        float sc;
+        lo = __ldg(st.lower + s);
+        step = __ldg(st.step + s);
+        m = __ldg(st.mean_id + s);
         if (ip) {
-          float acc = 0.0f;
-          for (int g = 0; g < groups; ++g) {
+          for (int g = sl; g < groups; g += S) {
             float c[8];
             group_codes(row, st.bits1, g, 8388608.0f + off, c);
-            float part = 0.0f;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) part = __fmaf_rn(qc[g * 8 + e], c[e], part);
-            acc += part;
+            for (int e = 0; e < 8; ++e) acc = __fmaf_rn(qc[g * 8 + e], c[e], acc);
           }
-          sc = __fmaf_rn(step, acc, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[m]));
         } else {
           const float* mu = st.means + (int64_t)m * d;
-          float acc = 0.0f;
-          for (int g = 0; g < groups; ++g) {
+          for (int g = sl; g < groups; g += S) {
             float c[8];
             group_codes(row, st.bits1, g, 8388608.0f, c);
-            float part = 0.0f;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-              const int j = g * 8 + e;
-              if (j < d) {
+              const int jj = g * 8 + e;
+              if (jj < d) {
                 float xh = __fmaf_rn(step, c[e], lo);
-                if (!one_mean) xh = __fadd_rn(xh, __ldg(mu + j));
-                const float df = qc[j] - xh;
-                part = __fmaf_rn(df, df, part);
+                if (!one_mean) xh = __fadd_rn(xh, __ldg(mu + jj));
+                const float df = qc[jj] - xh;
+                acc = __fmaf_rn(df, df, acc);
               }
             }
-            acc += part;
           }
-          sc = acc;
         }
+      }
+      // sum over the S lanes of each candidate (every lane takes part)
+      for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      if (ok && sl == 0) {
+        const float sc = ip ? __fmaf_rn(step, acc, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[m])) : acc;
         const uint64_t key = make_key(sc, (uint32_t)s, st.metric);
         if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
       }
