@@ -212,6 +212,10 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
   __shared__ int cnt;
   __shared__ uint64_t thr;
   __shared__ int scan_sh[kGatherThreads / 32 + 1];
+  // the round's candidates: slot id (-1: skipped) and per-row constants
+  __shared__ int64_t r_id[kGatherThreads];
+  __shared__ float r_lo[kGatherThreads], r_step[kGatherThreads];
+  __shared__ int r_m[kGatherThreads];
   const bool ip = st.metric == LVQ_IP;
   const bool one_mean = st.n_means == 1;
   for (int j = threadIdx.x; j < groups * 8; j += blockDim.x) {
@@ -228,34 +232,46 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
   const float qs = ip ? p.qsum[qi] : 0.0f;
   const float* cmq = ip ? p.cm + (int64_t)qi * st.n_means : nullptr;
   const int64_t* cl = cand + (int64_t)qi * n_cand;
-  // S lanes score one candidate (its code words spread over the lanes, so a
-  // row is read with a few wide loads); a warp scores 32 / S at a time
+  // Each round: the round's candidate ids and per-row constants are staged
+  // in shared memory by all threads (independent loads), then S lanes score
+  // one candidate (its code words spread over the lanes, so a row is read
+  // with a few wide loads), kC candidates per sub-warp in flight at once.
+  constexpr int kC = 4;
   const int S = groups >= 32 ? 32 : pow2_at_least(groups);
   const int per_warp = 32 / S;
   const int lane = threadIdx.x & 31, sub = lane / S, sl = lane % S;
   const int slot0 = (threadIdx.x >> 5) * per_warp + sub;
   const int nsub = (kGatherThreads / 32) * per_warp;
   for (int base = 0; base < n_cand; base += kGatherThreads) {
-    for (int j0 = 0; j0 < kGatherThreads; j0 += nsub) {
-      const int i = base + j0 + slot0;
+    {
+      const int i = base + threadIdx.x;
       const int64_t s = i < n_cand ? cl[i] : -1;
       const bool ok = s >= 0 && s < st.capacity && is_live(st.live, s);
-      float acc = 0.0f, lo = 0.0f, step = 0.0f;
-      int m = 0;
-      if (ok) {
+      r_id[threadIdx.x] = ok ? s : -1;
+      r_lo[threadIdx.x] = ok ? __ldg(st.lower + s) : 0.0f;
+      r_step[threadIdx.x] = ok ? __ldg(st.step + s) : 0.0f;
+      r_m[threadIdx.x] = ok ? __ldg(st.mean_id + s) : 0;
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < kGatherThreads; j0 += nsub * kC) {
+      float acc[kC];
+#pragma unroll
+      for (int u = 0; u < kC; ++u) {
+        acc[u] = 0.0f;
+        const int t = j0 + u * nsub + slot0;
+        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
+        if (s < 0) continue;
         const uint8_t* row = st.codes1 + s * st.row1;
-        lo = __ldg(st.lower + s);
-        step = __ldg(st.step + s);
-        m = __ldg(st.mean_id + s);
+        const float lo = r_lo[t], step = r_step[t];
         if (ip) {
           for (int g = sl; g < groups; g += S) {
             float c[8];
             group_codes(row, st.bits1, g, 8388608.0f + off, c);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc = __fmaf_rn(qc[g * 8 + e], c[e], acc);
+            for (int e = 0; e < 8; ++e) acc[u] = __fmaf_rn(qc[g * 8 + e], c[e], acc[u]);
           }
         } else {
-          const float* mu = st.means + (int64_t)m * d;
+          const float* mu = st.means + (int64_t)r_m[t] * d;
           for (int g = sl; g < groups; g += S) {
             float c[8];
             group_codes(row, st.bits1, g, 8388608.0f, c);
@@ -266,18 +282,25 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
                 float xh = __fmaf_rn(step, c[e], lo);
                 if (!one_mean) xh = __fadd_rn(xh, __ldg(mu + jj));
                 const float df = qc[jj] - xh;
-                acc = __fmaf_rn(df, df, acc);
+                acc[u] = __fmaf_rn(df, df, acc[u]);
               }
             }
           }
         }
       }
-      // sum over the S lanes of each candidate (every lane takes part)
-      for (int o = S >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-      if (ok && sl == 0) {
-        const float sc = ip ? __fmaf_rn(step, acc, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[m])) : acc;
-        const uint64_t key = make_key(sc, (uint32_t)s, st.metric);
-        if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+#pragma unroll
+      for (int u = 0; u < kC; ++u) {
+        // sum over the S lanes of each candidate (every lane takes part)
+        float a = acc[u];
+        for (int o = S >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+        const int t = j0 + u * nsub + slot0;
+        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
+        if (s >= 0 && sl == 0) {
+          const float step = r_step[t], lo = r_lo[t];
+          const float sc = ip ? __fmaf_rn(step, a, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[r_m[t]])) : a;
+          const uint64_t key = make_key(sc, (uint32_t)s, st.metric);
+          if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+        }
       }
     }
     __syncthreads();
