@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-recall", action="store_true", help="skip the oracle recall sample")
     ap.add_argument("--no-small", action="store_true", help="skip the small-batch roofline leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -353,6 +354,14 @@ def main():
     ins_dev = [torch.from_numpy(a).cuda() for a in ins_host]
     precision = args.precision
     st.reserve(nq, 100, C)
+    # the tensor-core scan's tile shape for this batch, chosen by the autotuner
+    # (query-tile widths 64 and 128, timed with the library's own events)
+    tuning = None
+    if not args.no_autotune and precision in ("auto", "fp16"):
+        from paper_2402_02044_b300 import autotune
+        best = autotune.autotune(st, q_dev, n, sizes=(nq,), k1=100, reps=1, widths=(64, 128), ctas_opts=(0,))
+        tuning = autotune.tuning_for(best, nq)
+        st.set_tuning(**tuning)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
 
@@ -508,7 +517,7 @@ def main():
                        "metric": "ip", "queries_per_step": int(nq), "query_batches": [int(v) for v in sizes],
                        "k1": 100, "k": 10, "gather_queries": nq_g, "gather_candidates": C,
                        "updates_per_step": B_upd, "l2_flush": "not needed: 3.9 GB of codes > 126 MB L2",
-                       "precision": precision},
+                       "precision": precision, "autotuned_tiles": tuning},
             "qps": qps, "recall_at_10": None, "small_batch": small, "serve": serve, "gather_roofline": gather_roof,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,

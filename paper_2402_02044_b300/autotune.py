@@ -27,12 +27,12 @@ def _key(store: "L.Store", n_rows: int) -> str:
     return f"{name}|d{store.d}|b{store.bits1}x{store.bits2}|{store.metric}|n{nb}"
 
 
-def candidates(nq: int, sm_count: int) -> list:
+def candidates(nq: int, sm_count: int, widths=(16, 32, 64, 128), ctas_opts=None) -> list:
     out = []
-    for n in (16, 32, 64, 128):
+    for n in widths:
         if n > 16 and n > 2 * max(nq, 1):
             continue
-        for ctas in (0, sm_count // 2):
+        for ctas in (ctas_opts if ctas_opts is not None else (0, sm_count // 2)):
             out.append({"mma_n": n, "mma_ctas": ctas})
     return out
 
@@ -53,7 +53,8 @@ def time_scan(store: "L.Store", q: torch.Tensor, k1: int, tuning: dict, reps: in
 
 
 def autotune(store: "L.Store", queries: torch.Tensor, n_rows: int, sizes: Iterable[int] = DEFAULT_SIZES,
-             k1: int = 100, reps: int = 3, cache_path: Optional[str] = None) -> dict:
+             k1: int = 100, reps: int = 3, cache_path: Optional[str] = None, widths=(16, 32, 64, 128),
+             ctas_opts=None) -> dict:
     """Best tuning per batch-size bucket: {bucket: {"mma_n": .., "mma_ctas": ..}}."""
     key = _key(store, n_rows)
     cache = {}
@@ -67,7 +68,7 @@ def autotune(store: "L.Store", queries: torch.Tensor, n_rows: int, sizes: Iterab
     for nq in sizes:
         q = queries[:nq].contiguous()
         timings = []
-        for t in candidates(nq, sm):
+        for t in candidates(nq, sm, widths, ctas_opts):
             try:
                 timings.append((time_scan(store, q, k1, t, reps), t))
             except L.LVQError:

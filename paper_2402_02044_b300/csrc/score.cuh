@@ -45,6 +45,28 @@ __device__ __forceinline__ void group_codes(const uint8_t* row, int bits1, int g
   }
 }
 
+// The same in two steps: the raw words of group g (one load), then their codes.
+__device__ __forceinline__ uint2 group_words(const uint8_t* row, int bits1, int g) {
+  if (bits1 == 4) return make_uint2(__ldg(reinterpret_cast<const uint32_t*>(row) + g), 0u);
+  return __ldg(reinterpret_cast<const uint2*>(row) + g);
+}
+__device__ __forceinline__ void words_codes(uint2 w, int bits1, float sub, float (&c)[8]) {
+  if (bits1 == 4) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const uint32_t t = nib_pair(w.x, p);
+      c[2 * p] = lo_centred(t, sub);
+      c[2 * p + 1] = hi_centred(t, sub);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c[i] = byte_centred(w.x, i, sub);
+      c[4 + i] = byte_centred(w.y, i, sub);
+    }
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);

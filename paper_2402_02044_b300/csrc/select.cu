@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
 // ---- ID-gather search (one block per query, one thread per candidate) ---------
 constexpr int kGatherThreads = 256;
 
-__global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, const float* __restrict__ q,
+__global__ void __launch_bounds__(kGatherThreads, 3) gather_kernel(DeviceStore st, const float* __restrict__ q,
                                                                  QueryPrep p, const int64_t* __restrict__ cand,
                                                                  int n_cand, int k1, int k, int rerank,
                                                                  int64_t* out_ids, float* out_scores) {
@@ -255,26 +255,38 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
     __syncthreads();
     for (int j0 = 0; j0 < kGatherThreads; j0 += nsub * kC) {
       float acc[kC];
+      // the first kGL groups of each lane for all kC candidates are loaded
+      // before any is used, so their loads are in flight together
+      constexpr int kGL = 4;
+      uint2 w[kC][kGL];
 #pragma unroll
       for (int u = 0; u < kC; ++u) {
         acc[u] = 0.0f;
         const int t = j0 + u * nsub + slot0;
         const int64_t s = t < kGatherThreads ? r_id[t] : -1;
+        const uint8_t* row = st.codes1 + (s < 0 ? 0 : s) * st.row1;
+#pragma unroll
+        for (int gi = 0; gi < kGL; ++gi) {
+          const int g = sl + gi * S;
+          w[u][gi] = (s >= 0 && g < groups) ? group_words(row, st.bits1, g) : make_uint2(0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kC; ++u) {
+        const int t = j0 + u * nsub + slot0;
+        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
         if (s < 0) continue;
         const uint8_t* row = st.codes1 + s * st.row1;
         const float lo = r_lo[t], step = r_step[t];
-        if (ip) {
-          for (int g = sl; g < groups; g += S) {
-            float c[8];
-            group_codes(row, st.bits1, g, 8388608.0f + off, c);
+        const float* mu = st.means + (int64_t)r_m[t] * d;
+        auto add_group = [&](uint2 ww, int g) {
+          float c[8];
+          if (ip) {
+            words_codes(ww, st.bits1, 8388608.0f + off, c);
 #pragma unroll
             for (int e = 0; e < 8; ++e) acc[u] = __fmaf_rn(qc[g * 8 + e], c[e], acc[u]);
-          }
-        } else {
-          const float* mu = st.means + (int64_t)r_m[t] * d;
-          for (int g = sl; g < groups; g += S) {
-            float c[8];
-            group_codes(row, st.bits1, g, 8388608.0f, c);
+          } else {
+            words_codes(ww, st.bits1, 8388608.0f, c);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int jj = g * 8 + e;
@@ -286,7 +298,11 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(DeviceStore st, 
               }
             }
           }
-        }
+        };
+#pragma unroll
+        for (int gi = 0; gi < kGL; ++gi)
+          if (sl + gi * S < groups) add_group(w[u][gi], sl + gi * S);
+        for (int g = sl + kGL * S; g < groups; g += S) add_group(group_words(row, st.bits1, g), g);
       }
 #pragma unroll
       for (int u = 0; u < kC; ++u) {
