@@ -126,6 +126,16 @@ cudaError_t launch_merge_rerank(const DeviceStore& st, const float* q, int64_t n
 cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                           const int64_t* ids, int k1, int k, int64_t* out_ids, float* out_scores,
                           cudaStream_t stream);
+// Geometry of the ID-gather kernel's row ring: R rows per batch (32 / R lanes
+// a row), slot stride (bytes), slot size, P slots per warp, dynamic shared
+// memory in bytes.
+struct GatherGeom {
+  int R, stride, slot_bytes, P;
+  size_t smem;
+};
+constexpr int kGatherSlotBudget = 3584;
+constexpr size_t kGatherSmemBudget = 220 * 1024;
+GatherGeom gather_geom(int row1, int d, int k1, int k, bool rerank);
 cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                           const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
                           float* out_scores, cudaStream_t stream);

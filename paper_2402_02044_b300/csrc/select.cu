@@ -3,6 +3,7 @@
 // greedy graph search, Alg. 1).
 #include "kernels.cuh"
 #include "score.cuh"
+#include "tcgen05.cuh"
 
 namespace lvq {
 
@@ -61,20 +62,122 @@ __global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* 
 
 // ---- shared re-rank tail -------------------------------------------------------
 // keys[0..n) hold candidate keys (sorted or not, possibly with repeats).  Each
-// warp scores candidates with both levels; the block then sorts the new keys
-// and writes the k best.  scratch: pow2_at_least(n) keys of shared memory.
-__device__ void rerank_tail(const DeviceStore& st, const float* qsh, const uint64_t* keys, int n, int k,
-                            uint64_t* scratch, int* sh_pos, int64_t* out_ids, float* out_scores) {
+// warp scores kRU candidates at a time with both levels, their code words for
+// the first kRG groups of each lane loaded before any is used, so the loads of
+// the candidates are in flight together; the block then sorts the new keys and
+// writes the k best.  With a single centring mean the mean is folded into the
+// query first: q - mu for L2 (qsh is overwritten), <q, mu> added once for the
+// inner product.  scratch: pow2_at_least(n) keys of shared memory.
+constexpr int kRU = 4;
+constexpr int kRG = 3;
+
+__device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* keys, int n, int k, uint64_t* scratch,
+                            int* sh_pos, int64_t* out_ids, float* out_scores) {
+  __shared__ float red_sh[33];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int d = st.d;
+  const int groups = (d + 7) >> 3;
+  const bool ip = st.metric == LVQ_IP;
+  const bool one_mean = st.n_means == 1;
   const int np2 = pow2_at_least(n < 1 ? 1 : n);
   for (int i = threadIdx.x; i < np2; i += blockDim.x) scratch[i] = kNoKey;
+  float c0 = 0.0f;
+  if (one_mean) {
+    float part = 0.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      const float mu = st.means[j];
+      if (ip)
+        part = __fmaf_rn(qsh[j], mu, part);
+      else
+        qsh[j] = __fsub_rn(qsh[j], mu);
+    }
+    if (ip) {
+      part = warp_sum(part);
+      if (lane == 0) red_sh[wid] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < nw; ++i) t += red_sh[i];
+        red_sh[32] = t;
+      }
+    }
+  }
   __syncthreads();
-  for (int i = wid; i < n; i += nw) {
-    const uint64_t key = keys[i];
-    if (key == kNoKey) continue;
-    const uint32_t s = (uint32_t)key;
-    const float sc = score2_warp(st, s, qsh);
-    if (lane == 0) scratch[i] = make_key(sc, s, st.metric);
+  if (one_mean && ip) c0 = red_sh[32];
+  for (int i0 = wid * kRU; i0 < n; i0 += nw * kRU) {
+    uint32_t sid[kRU];
+    bool ok[kRU];
+#pragma unroll
+    for (int u = 0; u < kRU; ++u) {
+      const uint64_t key = i0 + u < n ? keys[i0 + u] : kNoKey;
+      ok[u] = key != kNoKey;
+      sid[u] = (uint32_t)key;
+    }
+    // per-candidate constants, one lane each
+    float lo_l = 0.0f, st_l = 0.0f;
+    int m_l = 0;
+    {
+      const uint64_t key = (lane < kRU && i0 + lane < n) ? keys[i0 + lane] : kNoKey;
+      if (key != kNoKey) {
+        const uint32_t sl = (uint32_t)key;
+        lo_l = __ldg(st.lower + sl);
+        st_l = __ldg(st.step + sl);
+        m_l = __ldg(st.mean_id + sl);
+      }
+    }
+    uint2 w1[kRU][kRG], w2[kRU][kRG];
+#pragma unroll
+    for (int u = 0; u < kRU; ++u) {
+      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.row1;
+      const uint8_t* r2 = st.codes2 + (int64_t)sid[u] * st.row2;
+#pragma unroll
+      for (int gi = 0; gi < kRG; ++gi) {
+        const int g = lane + 32 * gi;
+        const bool in = ok[u] && g < groups;
+        w1[u][gi] = in ? group_words(r1, st.bits1, g) : make_uint2(0u, 0u);
+        w2[u][gi] = in ? __ldg(reinterpret_cast<const uint2*>(r2) + g) : make_uint2(0u, 0u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRU; ++u) {
+      const float lo = __shfl_sync(kFull, lo_l, u), step = __shfl_sync(kFull, st_l, u);
+      const int m = __shfl_sync(kFull, m_l, u);
+      if (!ok[u]) continue;
+      const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+      const float* mu = st.means + (int64_t)m * d;
+      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.row1;
+      const uint8_t* r2 = st.codes2 + (int64_t)sid[u] * st.row2;
+      float acc = 0.0f;
+      auto add_group = [&](uint2 a, uint2 b, int g) {
+        float c[8];
+        words_codes(a, st.bits1, 8388608.0f, c);
+        float part = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = g * 8 + e;
+          if (j < d) {
+            const float c2 = byte_centred(e < 4 ? b.x : b.y, e & 3, 8388608.0f);
+            float x2 = __fadd_rn(__fmaf_rn(step, c[e], lo), __fmaf_rn(step2, c2, lo2));
+            if (!one_mean) x2 = __fadd_rn(x2, __ldg(mu + j));
+            if (ip) {
+              part = __fmaf_rn(qsh[j], x2, part);
+            } else {
+              const float df = qsh[j] - x2;
+              part = __fmaf_rn(df, df, part);
+            }
+          }
+        }
+        acc += part;
+      };
+#pragma unroll
+      for (int gi = 0; gi < kRG; ++gi)
+        if (lane + 32 * gi < groups) add_group(w1[u][gi], w2[u][gi], lane + 32 * gi);
+      for (int g = lane + 32 * kRG; g < groups; g += 32)
+        add_group(group_words(r1, st.bits1, g), __ldg(reinterpret_cast<const uint2*>(r2) + g), g);
+      float sc = warp_sum(acc);
+      if (ip) sc = __fadd_rn(sc, c0);
+      if (lane == 0) scratch[i0 + u] = make_key(sc, sid[u], st.metric);
+    }
   }
   __syncthreads();
   block_sort(scratch, np2);
@@ -190,159 +293,286 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
   rerank_tail(st, qsh, keys, k1, k, scratch, sh_pos, out_ids + (int64_t)qi * k, out_scores + (int64_t)qi * k);
 }
 
-// ---- ID-gather search (one block per query, one thread per candidate) ---------
+// ---- ID-gather search (persistent blocks, one query at a time per block) ---------
+// Rows: each warp streams its share of a query's candidate rows (batches of R
+// rows, R = 32 / L) into its own ring of P shared-memory slots with bulk
+// copies completing on one mbarrier per slot, issuing P - 1 batches ahead of
+// the one it scores, across query boundaries too, so the next query's first
+// rows load while the block selects and re-ranks.  A row is scored by L lanes
+// (16-byte chunks l, l + L, ...); the slot stride makes the lanes of a
+// quarter warp hit distinct banks.
+// Products: <q, c> is computed exactly in integers: the query is rounded once
+// to 24-bit fixed point (Q_j = rint(q_j / s), s = max|q| / (2^23 - 1)), Q is
+// split into three byte planes (two unsigned, the top one signed) laid out in
+// code-word order, and dp4a accumulates each plane's products with the code
+// bytes in 32 bits; the planes are recombined in 64 bits, centred by the code
+// offset and scaled by s once per candidate.  Rounding q moves a score by at
+// most (s / 2) sqrt(d) ||x^|| <= 6e-8 sqrt(d) ||q|| ||x^||, a small fraction of
+// the float32 tolerance.
 constexpr int kGatherThreads = 256;
+constexpr int kGW = kGatherThreads / 32;
+constexpr uint32_t kGatherWaitLimit = 1u << 22;
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // an empty row of a batch
 
-__global__ void __launch_bounds__(kGatherThreads, 3) gather_kernel(DeviceStore st, const float* __restrict__ q,
-                                                                 QueryPrep p, const int64_t* __restrict__ cand,
-                                                                 int n_cand, int k1, int k, int rerank,
-                                                                 int64_t* out_ids, float* out_scores) {
+__device__ __forceinline__ uint32_t g_dp4a_uu(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int g_dp4a_us(uint32_t a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Dim (within its group of 8) of byte b of the query word that meets code
+// bytes in dp4a: for 4-bit codes half h = 0 pairs with (w & 0x0F0F0F0F),
+// dims (0, 4, 1, 5), h = 1 with ((w >> 4) & 0x0F0F0F0F), dims (2, 6, 3, 7);
+// for 8-bit codes half h is code word h, dims 4h..4h+3.
+__device__ __forceinline__ int plane_dim(int bits1, int h, int b) {
+  if (bits1 == 4) return (b >> 1) + 4 * (b & 1) + 2 * h;
+  return 4 * h + b;
+}
+
+struct GatherAcc {
+  uint32_t a0, a1;
+  int a2;
+};
+// one code group (two 32-bit words of code bytes) against the three planes
+__device__ __forceinline__ void plane_step(GatherAcc& A, uint32_t x0, uint32_t x1, uint2 p0, uint2 p1, uint2 p2) {
+  A.a0 = g_dp4a_uu(x0, p0.x, g_dp4a_uu(x1, p0.y, A.a0));
+  A.a1 = g_dp4a_uu(x0, p1.x, g_dp4a_uu(x1, p1.y, A.a1));
+  A.a2 = g_dp4a_us(x0, p2.x, g_dp4a_us(x1, p2.y, A.a2));
+}
+__device__ __forceinline__ void group4(GatherAcc& A, uint32_t w, uint2 p0, uint2 p1, uint2 p2) {
+  plane_step(A, w & 0x0F0F0F0Fu, (w >> 4) & 0x0F0F0F0Fu, p0, p1, p2);
+}
+
+__global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore st, const float* __restrict__ q,
+                                                                 int64_t nq, QueryPrep p,
+                                                                 const int64_t* __restrict__ cand, int n_cand, int k1,
+                                                                 int k, int rerank, GatherGeom gg, int64_t* out_ids,
+                                                                 float* out_scores) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int qi = blockIdx.x;
   const int d = st.d;
+  const int groups = (d + 7) >> 3, gpad = (groups + 3) & ~3;
   const int stage1 = rerank ? k1 : k;
   const int cap = pow2_at_least(stage1 + kGatherThreads);
-  const int groups = (d + 7) >> 3;
-  uint64_t* buf = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* scratch = buf + cap;
-  float* qsh = reinterpret_cast<float*>(scratch + pow2_at_least(stage1));
-  uint64_t* tmp = reinterpret_cast<uint64_t*>(qsh + groups * 8 * 2);  // cap keys
-  float* qc = qsh + groups * 8;  // centred / shifted copy used by the first level
-  int* sh_pos = reinterpret_cast<int*>(tmp + cap);
-  __shared__ int cnt;
+  const int R = gg.R, L = 32 / gg.R, P = gg.P;
+  unsigned char* slots = smem;  // [kGW][P][slot_bytes]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(slots + (size_t)kGW * P * gg.slot_bytes);  // [kGW][P]
+  uint32_t* slot_ids = reinterpret_cast<uint32_t*>(bars + kGW * P);                        // [kGW][P][32]
+  uint2* planes = reinterpret_cast<uint2*>(slot_ids + kGW * P * 32);                       // [3][gpad]
+  float* qsh = reinterpret_cast<float*>(planes + 3 * gpad);                                // [groups * 8]
+  uint64_t* buf = reinterpret_cast<uint64_t*>(qsh + groups * 8);                          // [cap]
+  uint64_t* tmp = buf + cap;                                                                // [cap]
+  uint64_t* scratch = tmp + cap;                        // [pow2_at_least(stage1)]
+  int* sh_pos = reinterpret_cast<int*>(scratch + pow2_at_least(stage1));  // [k + 2]
+  __shared__ int cnt, abort_sh;
   __shared__ uint64_t thr;
-  __shared__ int scan_sh[kGatherThreads / 32 + 1];
-  // the round's candidates: slot id (-1: skipped) and per-row constants
-  __shared__ int64_t r_id[kGatherThreads];
-  __shared__ float r_lo[kGatherThreads], r_step[kGatherThreads];
-  __shared__ int r_m[kGatherThreads];
+  __shared__ int scan_sh[kGW + 1];
+  __shared__ float qmax_sh[kGW];
+  __shared__ unsigned long long qsum_int;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool ip = st.metric == LVQ_IP;
-  const bool one_mean = st.n_means == 1;
-  for (int j = threadIdx.x; j < groups * 8; j += blockDim.x) {
-    const float v = j < d ? q[(int64_t)qi * d + j] : 0.0f;
-    qsh[j] = v;
-    qc[j] = (!ip && one_mean && j < d) ? __fsub_rn(v, st.means[j]) : v;
-  }
+  const bool b4 = st.bits1 == 4;
+  const int nchunks = b4 ? gpad / 4 : (groups + 1) / 2;
+  const int nb = (n_cand + R - 1) / R;  // batches of a query
+  const int rounds = (nb + kGW - 1) / kGW;
+  const int per_q = nb > w ? (nb - w + kGW - 1) / kGW : 0;  // this warp's batches of a query
+  const int64_t my_q = nq > (int64_t)blockIdx.x ? (nq - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t items = (int64_t)per_q * my_q;
   if (threadIdx.x == 0) {
-    cnt = 0;
-    thr = kNoKey;
+    for (int i = 0; i < kGW * P; ++i) sm100::mbar_init(bars + i, 1);
+    sm100::fence_mbar_init();
+    abort_sh = 0;
   }
   __syncthreads();
+  int64_t issued = 0, consumed = 0;  // this warp's items
+  // item t of this warp: query blockIdx.x + (t / per_q) * gridDim.x, batch w + (t % per_q) * kGW
+  auto issue = [&](int64_t t) {
+    if (t >= items) return;
+    const int slot = (int)(t % P);
+    const int64_t qi = blockIdx.x + (t / per_q) * gridDim.x;
+    const int b = w + (int)(t % per_q) * kGW;
+    int64_t s = -1;
+    if (lane < R) {
+      const int i = b * R + lane;
+      if (i < n_cand) {
+        s = cand[qi * n_cand + i];
+        if (s < 0 || s >= st.capacity) s = -1;
+      }
+      slot_ids[(w * P + slot) * 32 + lane] = s < 0 ? kNoSlot : (uint32_t)s;
+    }
+    const unsigned vm = __ballot_sync(kFull, s >= 0);
+    uint64_t* bar = bars + w * P + slot;
+    sm100::fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) sm100::mbar_expect_tx(bar, (uint32_t)__popc(vm) * (uint32_t)st.row1);
+    __syncwarp();
+    if (s >= 0)
+      sm100::bulk_load(slots + (size_t)(w * P + slot) * gg.slot_bytes + (size_t)lane * gg.stride,
+                       st.codes1 + s * st.row1, (uint32_t)st.row1, bar);
+    issued = t + 1;
+  };
+  // Per-row constants of the next item, loaded one item ahead by the first
+  // lane of each row so that their latency hides behind a batch's products.
+  const int r = lane / L, l = lane % L;
+  bool pf_live = false;
+  float pf_lo = 0.0f, pf_stp = 0.0f, pf_nrm = 0.0f;
+  int pf_m = 0;
+  auto load_consts = [&](int64_t t) {
+    pf_live = false;
+    if (t >= issued || l != 0) return;
+    const uint32_t su = slot_ids[(w * P + (int)(t % P)) * 32 + r];
+    if (su == kNoSlot) return;
+    pf_live = is_live(st.live, su);
+    pf_lo = __ldg(st.lower + su);
+    pf_stp = __ldg(st.step + su);
+    pf_m = __ldg(st.mean_id + su);
+    pf_nrm = ip ? 0.0f : __ldg(st.norm2 + su);
+  };
+  for (int64_t t = 0; t < P - 1; ++t) issue(t);
+  load_consts(0);
+  const int ioff = b4 ? 8 : 128;
   const float off = code_offset(st.bits1);
-  const float qs = ip ? p.qsum[qi] : 0.0f;
-  const float* cmq = ip ? p.cm + (int64_t)qi * st.n_means : nullptr;
-  const int64_t* cl = cand + (int64_t)qi * n_cand;
-  // Each round: the round's candidate ids and per-row constants are staged
-  // in shared memory by all threads (independent loads), then S lanes score
-  // one candidate (its code words spread over the lanes, so a row is read
-  // with a few wide loads), kC candidates per sub-warp in flight at once.
-  constexpr int kC = 4;
-  const int S = groups >= 32 ? 32 : pow2_at_least(groups);
-  const int per_warp = 32 / S;
-  const int lane = threadIdx.x & 31, sub = lane / S, sl = lane % S;
-  const int slot0 = (threadIdx.x >> 5) * per_warp + sub;
-  const int nsub = (kGatherThreads / 32) * per_warp;
-  for (int base = 0; base < n_cand; base += kGatherThreads) {
-    {
-      const int i = base + threadIdx.x;
-      const int64_t s = i < n_cand ? cl[i] : -1;
-      const bool ok = s >= 0 && s < st.capacity && is_live(st.live, s);
-      r_id[threadIdx.x] = ok ? s : -1;
-      r_lo[threadIdx.x] = ok ? __ldg(st.lower + s) : 0.0f;
-      r_step[threadIdx.x] = ok ? __ldg(st.step + s) : 0.0f;
-      r_m[threadIdx.x] = ok ? __ldg(st.mean_id + s) : 0;
+  for (int64_t qk = 0; qk < my_q; ++qk) {
+    const int64_t qi = blockIdx.x + qk * gridDim.x;
+    // ---- the query's byte planes
+    const float* qrow = q + qi * d;
+    float mx = 0.0f;
+    for (int j = threadIdx.x; j < groups * 8; j += blockDim.x) {
+      const float v = j < d ? qrow[j] : 0.0f;
+      qsh[j] = v;
+      mx = fmaxf(mx, fabsf(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    if (lane == 0) qmax_sh[w] = mx;
+    if (threadIdx.x == 0) {
+      cnt = 0;
+      thr = kNoKey;
+      qsum_int = 0ull;
     }
     __syncthreads();
-    for (int j0 = 0; j0 < kGatherThreads; j0 += nsub * kC) {
-      float acc[kC];
-      // the first kGL groups of each lane for all kC candidates are loaded
-      // before any is used, so their loads are in flight together
-      constexpr int kGL = 4;
-      uint2 w[kC][kGL];
+    mx = 0.0f;
 #pragma unroll
-      for (int u = 0; u < kC; ++u) {
-        acc[u] = 0.0f;
-        const int t = j0 + u * nsub + slot0;
-        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
-        const uint8_t* row = st.codes1 + (s < 0 ? 0 : s) * st.row1;
+    for (int i = 0; i < kGW; ++i) mx = fmaxf(mx, qmax_sh[i]);
+    const float qscale = mx > 0.0f ? mx / 8388607.0f : 0.0f;
+    const float qinv = mx > 0.0f ? 8388607.0f / mx : 0.0f;
+    {
+      long long part = 0;
+      for (int g = threadIdx.x; g < gpad; g += blockDim.x) {
+        uint32_t pw[3][2];
 #pragma unroll
-        for (int gi = 0; gi < kGL; ++gi) {
-          const int g = sl + gi * S;
-          w[u][gi] = (s >= 0 && g < groups) ? group_words(row, st.bits1, g) : make_uint2(0u, 0u);
+        for (int h = 0; h < 2; ++h) {
+          pw[0][h] = pw[1][h] = pw[2][h] = 0u;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int j = 8 * g + plane_dim(st.bits1, h, b);
+            const int v = j < d ? max(-8388607, min(8388607, __float2int_rn(qsh[j] * qinv))) : 0;
+            part += v;
+            pw[0][h] |= (uint32_t)(v & 255) << (8 * b);
+            pw[1][h] |= (uint32_t)((v >> 8) & 255) << (8 * b);
+            pw[2][h] |= (uint32_t)((v >> 16) & 255) << (8 * b);
+          }
         }
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) planes[pl * gpad + g] = make_uint2(pw[pl][0], pw[pl][1]);
       }
-#pragma unroll
-      for (int u = 0; u < kC; ++u) {
-        const int t = j0 + u * nsub + slot0;
-        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
-        if (s < 0) continue;
-        const uint8_t* row = st.codes1 + s * st.row1;
-        const float lo = r_lo[t], step = r_step[t];
-        const float* mu = st.means + (int64_t)r_m[t] * d;
-        auto add_group = [&](uint2 ww, int g) {
-          float c[8];
-          if (ip) {
-            words_codes(ww, st.bits1, 8388608.0f + off, c);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) acc[u] = __fmaf_rn(qc[g * 8 + e], c[e], acc[u]);
-          } else {
-            words_codes(ww, st.bits1, 8388608.0f, c);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int jj = g * 8 + e;
-              if (jj < d) {
-                float xh = __fmaf_rn(step, c[e], lo);
-                if (!one_mean) xh = __fadd_rn(xh, __ldg(mu + jj));
-                const float df = qc[jj] - xh;
-                acc[u] = __fmaf_rn(df, df, acc[u]);
+      if (part != 0) atomicAdd(&qsum_int, (unsigned long long)part);
+    }
+    __syncthreads();
+    // <Q, c - off> = <Q, c> - off * sum(Q)
+    const long long qoff = (long long)qsum_int * ioff;
+    const float qs = p.qsum[qi];
+    const float qn = ip ? 0.0f : p.qnorm[qi];
+    const float* cmq = p.cm + qi * st.n_means;
+    const uint4* pl4 = reinterpret_cast<const uint4*>(planes);
+    const int pstride4 = gpad / 2;  // uint4 per plane
+    for (int rd = 0; rd < rounds; ++rd) {
+      if (rd < per_q && !__shfl_sync(kFull, abort_sh, 0)) {
+        const int64_t t = qk * per_q + rd;
+        issue(t + P - 1);
+        const int slot = (int)(t % P);
+        const bool ok = sm100::mbar_wait(bars + w * P + slot, (uint32_t)((t / P) & 1), kGatherWaitLimit);
+        if (!__all_sync(kFull, ok)) {
+          if (lane == 0) {
+            abort_sh = 1;
+            set_error(st.err, LVQ_ETIMEOUT);
+          }
+        } else {
+          const uint32_t su = slot_ids[(w * P + slot) * 32 + r];
+          const bool live = pf_live;
+          const float lo = pf_lo, stp = pf_stp, nrm = pf_nrm;
+          const int m = pf_m;
+          load_consts(t + 1);
+          GatherAcc A{0u, 0u, 0};
+          if (su != kNoSlot) {
+            const uint4* row = reinterpret_cast<const uint4*>(slots + (size_t)(w * P + slot) * gg.slot_bytes +
+                                                              (size_t)r * gg.stride);
+            for (int c = l; c < nchunks; c += L) {
+              const uint4 cw = row[c];
+              if (b4) {
+                const uint4 a0 = pl4[2 * c], a1 = pl4[2 * c + 1];
+                const uint4 b0 = pl4[pstride4 + 2 * c], b1 = pl4[pstride4 + 2 * c + 1];
+                const uint4 c0 = pl4[2 * pstride4 + 2 * c], c1 = pl4[2 * pstride4 + 2 * c + 1];
+                group4(A, cw.x, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
+                group4(A, cw.y, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
+                group4(A, cw.z, make_uint2(a1.x, a1.y), make_uint2(b1.x, b1.y), make_uint2(c1.x, c1.y));
+                group4(A, cw.w, make_uint2(a1.z, a1.w), make_uint2(b1.z, b1.w), make_uint2(c1.z, c1.w));
+              } else {
+                const uint4 a0 = pl4[c], b0 = pl4[pstride4 + c], c0 = pl4[2 * pstride4 + c];
+                plane_step(A, cw.x, cw.y, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
+                plane_step(A, cw.z, cw.w, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
               }
             }
           }
-        };
-#pragma unroll
-        for (int gi = 0; gi < kGL; ++gi)
-          if (sl + gi * S < groups) add_group(w[u][gi], sl + gi * S);
-        for (int g = sl + kGL * S; g < groups; g += S) add_group(group_words(row, st.bits1, g), g);
-      }
-#pragma unroll
-      for (int u = 0; u < kC; ++u) {
-        // sum over the S lanes of each candidate (every lane takes part)
-        float a = acc[u];
-        for (int o = S >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
-        const int t = j0 + u * nsub + slot0;
-        const int64_t s = t < kGatherThreads ? r_id[t] : -1;
-        if (s >= 0 && sl == 0) {
-          const float step = r_step[t], lo = r_lo[t];
-          const float sc = ip ? __fmaf_rn(step, a, __fmaf_rn(__fmaf_rn(off, step, lo), qs, cmq[r_m[t]])) : a;
-          const uint64_t key = make_key(sc, (uint32_t)s, st.metric);
-          if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+          // the L lanes of a row are consecutive
+          for (int o = L >> 1; o > 0; o >>= 1) {
+            A.a0 += __shfl_xor_sync(kFull, A.a0, o);
+            A.a1 += __shfl_xor_sync(kFull, A.a1, o);
+            A.a2 += __shfl_xor_sync(kFull, A.a2, o);
+          }
+          if (l == 0 && live) {
+            const long long dot = (long long)A.a0 + ((long long)A.a1 << 8) + ((long long)A.a2 << 16) - qoff;
+            const float a = __fmul_rn(qscale, (float)dot);
+            float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo), qs, cmq[m]));
+            if (!ip) sc = __fadd_rn(__fadd_rn(qn, nrm), -2.0f * sc);
+            const uint64_t key = make_key(sc, su, st.metric);
+            if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+          }
+          consumed = t + 1;
+          __syncwarp();
         }
       }
+      __syncthreads();
+      if (cnt > cap - kGatherThreads) {
+        uint64_t t;
+        const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
+        if (threadIdx.x == 0) {
+          cnt = kept;
+          thr = t;
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
-    if (cnt > cap - kGatherThreads) {
+    {
       uint64_t t;
       const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
-      if (threadIdx.x == 0) {
-        cnt = kept;
-        thr = t;
-      }
+      if (threadIdx.x == 0) cnt = kept;
       __syncthreads();
     }
+    int64_t* oi = out_ids + qi * k;
+    float* os = out_scores + qi * k;
+    if (!rerank)
+      write_results(buf, cnt, k, st.metric, oi, os, sh_pos);
+    else
+      rerank_tail(st, qsh, buf, cnt, k, scratch, sh_pos, oi, os);
   }
-  {
-    uint64_t t;
-    const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
-    if (threadIdx.x == 0) cnt = kept;
-    __syncthreads();
-  }
-  int64_t* oi = out_ids + (int64_t)qi * k;
-  float* os = out_scores + (int64_t)qi * k;
-  if (!rerank) {
-    write_results(buf, cnt, k, st.metric, oi, os, sh_pos);
-    return;
-  }
-  rerank_tail(st, qsh, buf, cnt, k, scratch, sh_pos, oi, os);
+  // copies still in flight (after an abort) land before the block exits
+  for (int64_t t = consumed; t < issued; ++t)
+    sm100::mbar_wait(bars + w * P + (int)(t % P), (uint32_t)((t / P) & 1), kGatherWaitLimit);
 }
 
 }  // namespace
@@ -401,21 +631,50 @@ cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, con
   return cudaGetLastError();
 }
 
+GatherGeom gather_geom(int row1, int d, int k1, int k, bool rerank) {
+  GatherGeom g{};
+  const int r16 = row1 / 16;
+  for (int R = 32; R >= 1; R >>= 1) {
+    const int L = 32 / R;
+    int s16 = r16;
+    if (L < 8)
+      while (s16 % (2 * L) != L) ++s16;  // the rows of a quarter warp start in distinct banks
+    g.R = R;
+    g.stride = s16 * 16;
+    g.slot_bytes = R * g.stride;
+    if (g.slot_bytes <= kGatherSlotBudget) break;
+  }
+  const int stage1 = rerank ? k1 : k;
+  const int groups = (d + 7) / 8, gpad = (groups + 3) & ~3;
+  const size_t rest = (size_t)(2 * pow2_at_least(stage1 + kGatherThreads) + pow2_at_least(stage1)) * 8 +
+                      (size_t)gpad * 3 * 8 + (size_t)groups * 8 * 4 + (size_t)(k + 2) * 4 + 16;
+  for (g.P = 3; g.P > 2; --g.P)
+    if ((size_t)kGW * g.P * (g.slot_bytes + 8 + 32 * 4) + rest <= kGatherSmemBudget) break;
+  g.smem = (size_t)kGW * g.P * (g.slot_bytes + 8 + 32 * 4) + rest;
+  return g;
+}
+
 cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                           const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
                           float* out_scores, cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
-  const int stage1 = rerank ? k1 : k;
-  const int groups = (st.d + 7) / 8;
-  const size_t sm = (size_t)(2 * pow2_at_least(stage1 + kGatherThreads) + pow2_at_least(stage1)) * 8 +
-                    (size_t)groups * 8 * 4 * 2 + (size_t)(k + 2) * 4 + 16;
+  const GatherGeom g = gather_geom(st.row1, st.d, k1, k, rerank);
+  if (g.smem > kGatherSmemBudget) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGatherSmemBudget);
+    if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  gather_kernel<<<(unsigned)nq, kGatherThreads, sm, stream>>>(st, q, p, cand, n_cand, k1, k, rerank ? 1 : 0,
-                                                              out_ids, out_scores);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_kernel, kGatherThreads, g.smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t grid = std::min<int64_t>(nq, (int64_t)sms * per_sm);
+  gather_kernel<<<(unsigned)grid, kGatherThreads, g.smem, stream>>>(st, q, nq, p, cand, n_cand, k1, k,
+                                                                   rerank ? 1 : 0, g, out_ids, out_scores);
   return cudaGetLastError();
 }
 

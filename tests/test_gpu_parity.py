@@ -13,7 +13,7 @@ import torch
 
 import oracle as O
 import synth
-from helpers import (TOL_FP32, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
+from helpers import (TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
                      lib_store)
 
 pytestmark = pytest.mark.gpu
@@ -204,6 +204,51 @@ def test_candidates_and_rerank(metric):
     for i in range(nq):
         mism = set(ri[i].tolist()) ^ set(ref_i[i].tolist())
         assert len(mism) <= 2
+    st.close()
+
+
+GATHER_CASES = [
+    # n, d, comps, metric, bits1, bits2, n_means, nq, C, k1, k
+    (20000, 768, 32, "ip", 4, 8, 1, 24, 1000, 100, 10),
+    (20000, 768, 32, "l2", 8, 8, 4, 24, 700, 50, 10),
+    (6000, 100, 16, "l2", 4, 8, 1, 40, 500, 40, 7),      # ragged d, 16 lanes a candidate
+    (3000, 4096, 8, "ip", 4, 8, 1, 6, 300, 30, 10),      # groups beyond the preloaded ones
+    (3000, 4096, 8, "l2", 8, 0, 1, 4, 200, 0, 10),       # LVQ-8 single level, largest d
+    (4000, 24, 8, "l2", 8, 0, 1, 32, 300, 0, 10),        # 4 lanes a candidate
+    (8000, 64, 16, "ip", 4, 8, 256, 32, 600, 60, 10),    # the most centres
+    (5000, 96, 16, "ip", 4, 0, 1, 16, 2048, 0, 20),      # many rounds
+]
+
+
+def _gid(c):
+    return "n%d-d%d-%s-%dx%d-M%d-C%d-k%d" % (c[0], c[1], c[3], c[4], c[5], c[6], c[8], c[9])
+
+
+@pytest.mark.parametrize("case", GATHER_CASES, ids=_gid)
+def test_candidates_widths_dims_means(case):
+    """ID-gather search over code widths, dimensionalities (sub-warp sizes 4
+    to 32 lanes, rows longer than the preloaded groups), centring means and
+    both metrics: first-level scores within the float32 tolerance, ids equal
+    to the oracle's up to near-ties."""
+    n, d, comps, metric, b1, b2, m, nq, C, k1, k = case
+    x, q, means = gmm_case(n, d, comps, metric, nq, seed=700 + d + m, n_means=m)
+    st, ids = lib_store(x, means, b1, b2, metric)
+    mid = st.export(ids)["mean_id"].cpu().numpy()
+    enc = O.encode(x, means, b1, b2, mean_id=mid)
+    g = np.random.default_rng(d + C)
+    cand = g.integers(0, n, (nq, C)).astype(np.int64)
+    cand[:, 1] = cand[:, 0]          # a repeat
+    cand[:, 2] = -1                  # skipped
+    qt, ct = torch.from_numpy(q).cuda(), torch.from_numpy(cand).cuda()
+    gi, gs = st.search_candidates(qt, ct, k, k1)
+    check_sorted(gs, metric)
+    if k1 and b2:
+        check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
+        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP32, cand_ids=cand)
+    else:
+        check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP32)
+        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP32, cand_ids=cand)
+    check_no_device_error(st)
     st.close()
 
 
