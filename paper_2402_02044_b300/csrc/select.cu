@@ -3,7 +3,6 @@
 // greedy graph search, Alg. 1).
 #include "kernels.cuh"
 #include "score.cuh"
-#include "tcgen05.cuh"
 
 namespace lvq {
 
@@ -295,12 +294,13 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
 
 // ---- ID-gather search (persistent blocks, one query at a time per block) ---------
 // Rows: each warp streams its share of a query's candidate rows (batches of R
-// rows, R = 32 / L) into its own ring of P shared-memory slots with bulk
-// copies completing on one mbarrier per slot, issuing P - 1 batches ahead of
-// the one it scores, across query boundaries too, so the next query's first
-// rows load while the block selects and re-ranks.  A row is scored by L lanes
-// (16-byte chunks l, l + L, ...); the slot stride makes the lanes of a
-// quarter warp hit distinct banks.
+// rows, R = 32 / L) into its own ring of P shared-memory slots with 16-byte
+// cp.async copies (one commit group per batch; the lanes of a warp copy
+// consecutive chunks of a row, so every row is read with coalesced requests),
+// issuing P - 1 batches ahead of the one it scores, across query boundaries
+// too, so the next query's first rows load while the block selects and
+// re-ranks.  A row is scored by L lanes (16-byte chunks l, l + L, ...); the
+// slot stride makes the lanes of a quarter warp hit distinct banks.
 // Products: <q, c> is computed exactly in integers: the query is rounded once
 // to 24-bit fixed point (Q_j = rint(q_j / s), s = max|q| / (2^23 - 1)), Q is
 // split into three byte planes (two unsigned, the top one signed) laid out in
@@ -311,7 +311,6 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
 // the float32 tolerance.
 constexpr int kGatherThreads = 256;
 constexpr int kGW = kGatherThreads / 32;
-constexpr uint32_t kGatherWaitLimit = 1u << 22;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // an empty row of a batch
 
 __device__ __forceinline__ uint32_t g_dp4a_uu(uint32_t a, uint32_t b, uint32_t c) {
@@ -332,6 +331,17 @@ __device__ __forceinline__ int g_dp4a_us(uint32_t a, uint32_t b, int c) {
 __device__ __forceinline__ int plane_dim(int bits1, int h, int b) {
   if (bits1 == 4) return (b >> 1) + 4 * (b & 1) + 2 * h;
   return 4 * h + b;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 struct GatherAcc {
@@ -360,15 +370,14 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   const int cap = pow2_at_least(stage1 + kGatherThreads);
   const int R = gg.R, L = 32 / gg.R, P = gg.P;
   unsigned char* slots = smem;  // [kGW][P][slot_bytes]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(slots + (size_t)kGW * P * gg.slot_bytes);  // [kGW][P]
-  uint32_t* slot_ids = reinterpret_cast<uint32_t*>(bars + kGW * P);                        // [kGW][P][32]
+  uint32_t* slot_ids = reinterpret_cast<uint32_t*>(slots + (size_t)kGW * P * gg.slot_bytes);  // [kGW][P][32]
   uint2* planes = reinterpret_cast<uint2*>(slot_ids + kGW * P * 32);                       // [3][gpad]
   float* qsh = reinterpret_cast<float*>(planes + 3 * gpad);                                // [groups * 8]
   uint64_t* buf = reinterpret_cast<uint64_t*>(qsh + groups * 8);                          // [cap]
   uint64_t* tmp = buf + cap;                                                                // [cap]
   uint64_t* scratch = tmp + cap;                        // [pow2_at_least(stage1)]
   int* sh_pos = reinterpret_cast<int*>(scratch + pow2_at_least(stage1));  // [k + 2]
-  __shared__ int cnt, abort_sh;
+  __shared__ int cnt;
   __shared__ uint64_t thr;
   __shared__ int scan_sh[kGW + 1];
   __shared__ float qmax_sh[kGW];
@@ -382,38 +391,46 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   const int per_q = nb > w ? (nb - w + kGW - 1) / kGW : 0;  // this warp's batches of a query
   const int64_t my_q = nq > (int64_t)blockIdx.x ? (nq - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const int64_t items = (int64_t)per_q * my_q;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kGW * P; ++i) sm100::mbar_init(bars + i, 1);
-    sm100::fence_mbar_init();
-    abort_sh = 0;
-  }
-  __syncthreads();
-  int64_t issued = 0, consumed = 0;  // this warp's items
-  // item t of this warp: query blockIdx.x + (t / per_q) * gridDim.x, batch w + (t % per_q) * kGW
-  auto issue = [&](int64_t t) {
-    if (t >= items) return;
-    const int slot = (int)(t % P);
-    const int64_t qi = blockIdx.x + (t / per_q) * gridDim.x;
-    const int b = w + (int)(t % per_q) * kGW;
-    int64_t s = -1;
-    if (lane < R) {
-      const int i = b * R + lane;
-      if (i < n_cand) {
-        s = cand[qi * n_cand + i];
-        if (s < 0 || s >= st.capacity) s = -1;
+  const int r16 = st.row1 / 16;
+  const uint32_t r16_magic = 0xFFFFFFFFu / (uint32_t)r16 + 1u;  // c / r16 == umulhi(c, magic) for c < 2^13
+  // This warp's items in order: query blockIdx.x + qk * gridDim.x, batch
+  // w + rd * kGW for rd < per_q.  Every issue commits one group (empty past
+  // the last item), so waiting for all but the newest P - 1 groups completes
+  // the oldest.
+  int64_t i_n = 0, i_qk = 0;  // items issued; query iteration of the next one
+  int i_rd = 0, i_slot = 0;
+  auto issue_next = [&]() {
+    if (i_n < items) {
+      const int slot = i_slot;
+      const int64_t qi = blockIdx.x + i_qk * gridDim.x;
+      const int b = w + i_rd * kGW;
+      int64_t s = -1;
+      if (lane < R) {
+        const int i = b * R + lane;
+        if (i < n_cand) {
+          s = cand[qi * n_cand + i];
+          if (s < 0 || s >= st.capacity) s = -1;
+        }
+        slot_ids[(w * P + slot) * 32 + lane] = s < 0 ? kNoSlot : (uint32_t)s;
       }
-      slot_ids[(w * P + slot) * 32 + lane] = s < 0 ? kNoSlot : (uint32_t)s;
+      unsigned char* base = slots + (size_t)(w * P + slot) * gg.slot_bytes;
+      // chunk c of the batch: row c / r16, column c % r16 (the same trip count
+      // on every lane, so that the shuffle has all of them)
+      for (int c0 = 0; c0 < R * r16; c0 += 32) {
+        const int c = c0 + lane;
+        const int row = (int)__umulhi((uint32_t)c, r16_magic), col = c - row * r16;
+        const bool in = c < R * r16;
+        const int64_t sr = __shfl_sync(kFull, s, in ? row : 0);
+        if (in && sr >= 0) cp_async16(base + (size_t)row * gg.stride + 16 * col, st.codes1 + sr * st.row1 + 16 * col);
+      }
+      ++i_n;
+      if (++i_rd == per_q) {
+        i_rd = 0;
+        ++i_qk;
+      }
+      i_slot = i_slot + 1 == P ? 0 : i_slot + 1;
     }
-    const unsigned vm = __ballot_sync(kFull, s >= 0);
-    uint64_t* bar = bars + w * P + slot;
-    sm100::fence_proxy_async_smem();
-    __syncwarp();
-    if (lane == 0) sm100::mbar_expect_tx(bar, (uint32_t)__popc(vm) * (uint32_t)st.row1);
-    __syncwarp();
-    if (s >= 0)
-      sm100::bulk_load(slots + (size_t)(w * P + slot) * gg.slot_bytes + (size_t)lane * gg.stride,
-                       st.codes1 + s * st.row1, (uint32_t)st.row1, bar);
-    issued = t + 1;
+    cp_async_commit();
   };
   // Per-row constants of the next item, loaded one item ahead by the first
   // lane of each row so that their latency hides behind a batch's products.
@@ -421,10 +438,10 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   bool pf_live = false;
   float pf_lo = 0.0f, pf_stp = 0.0f, pf_nrm = 0.0f;
   int pf_m = 0;
-  auto load_consts = [&](int64_t t) {
+  auto load_consts = [&](int64_t t, int slot) {
     pf_live = false;
-    if (t >= issued || l != 0) return;
-    const uint32_t su = slot_ids[(w * P + (int)(t % P)) * 32 + r];
+    if (t >= i_n || l != 0) return;
+    const uint32_t su = slot_ids[(w * P + slot) * 32 + r];
     if (su == kNoSlot) return;
     pf_live = is_live(st.live, su);
     pf_lo = __ldg(st.lower + su);
@@ -432,8 +449,11 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     pf_m = __ldg(st.mean_id + su);
     pf_nrm = ip ? 0.0f : __ldg(st.norm2 + su);
   };
-  for (int64_t t = 0; t < P - 1; ++t) issue(t);
-  load_consts(0);
+  for (int i = 0; i < P - 1; ++i) issue_next();
+  __syncwarp();
+  load_consts(0, 0);
+  int64_t c_n = 0;  // items consumed
+  int c_slot = 0;
   const int ioff = b4 ? 8 : 128;
   const float off = code_offset(st.bits1);
   for (int64_t qk = 0; qk < my_q; ++qk) {
@@ -491,22 +511,22 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     const uint4* pl4 = reinterpret_cast<const uint4*>(planes);
     const int pstride4 = gpad / 2;  // uint4 per plane
     for (int rd = 0; rd < rounds; ++rd) {
-      if (rd < per_q && !__shfl_sync(kFull, abort_sh, 0)) {
-        const int64_t t = qk * per_q + rd;
-        issue(t + P - 1);
-        const int slot = (int)(t % P);
-        const bool ok = sm100::mbar_wait(bars + w * P + slot, (uint32_t)((t / P) & 1), kGatherWaitLimit);
-        if (!__all_sync(kFull, ok)) {
-          if (lane == 0) {
-            abort_sh = 1;
-            set_error(st.err, LVQ_ETIMEOUT);
-          }
-        } else {
+      if (rd < per_q) {
+        issue_next();
+        const int slot = c_slot;
+        if (P == 3)
+          cp_async_wait<2>();
+        else
+          cp_async_wait<1>();
+        __syncwarp();
+        {
           const uint32_t su = slot_ids[(w * P + slot) * 32 + r];
           const bool live = pf_live;
           const float lo = pf_lo, stp = pf_stp, nrm = pf_nrm;
           const int m = pf_m;
-          load_consts(t + 1);
+          c_slot = c_slot + 1 == P ? 0 : c_slot + 1;
+          ++c_n;
+          load_consts(c_n, c_slot);
           GatherAcc A{0u, 0u, 0};
           if (su != kNoSlot) {
             const uint4* row = reinterpret_cast<const uint4*>(slots + (size_t)(w * P + slot) * gg.slot_bytes +
@@ -542,7 +562,6 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
             const uint64_t key = make_key(sc, su, st.metric);
             if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
           }
-          consumed = t + 1;
           __syncwarp();
         }
       }
@@ -570,9 +589,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     else
       rerank_tail(st, qsh, buf, cnt, k, scratch, sh_pos, oi, os);
   }
-  // copies still in flight (after an abort) land before the block exits
-  for (int64_t t = consumed; t < issued; ++t)
-    sm100::mbar_wait(bars + w * P + (int)(t % P), (uint32_t)((t / P) & 1), kGatherWaitLimit);
+  cp_async_wait<0>();
 }
 
 }  // namespace
@@ -649,8 +666,8 @@ GatherGeom gather_geom(int row1, int d, int k1, int k, bool rerank) {
   const size_t rest = (size_t)(2 * pow2_at_least(stage1 + kGatherThreads) + pow2_at_least(stage1)) * 8 +
                       (size_t)gpad * 3 * 8 + (size_t)groups * 8 * 4 + (size_t)(k + 2) * 4 + 16;
   for (g.P = 3; g.P > 2; --g.P)
-    if ((size_t)kGW * g.P * (g.slot_bytes + 8 + 32 * 4) + rest <= kGatherSmemBudget) break;
-  g.smem = (size_t)kGW * g.P * (g.slot_bytes + 8 + 32 * 4) + rest;
+    if ((size_t)kGW * g.P * (g.slot_bytes + 32 * 4) + rest <= kGatherSmemBudget) break;
+  g.smem = (size_t)kGW * g.P * (g.slot_bytes + 32 * 4) + rest;
   return g;
 }
 
