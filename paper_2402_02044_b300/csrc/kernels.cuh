@@ -133,11 +133,11 @@ struct GatherGeom {
   int R, stride, slot_bytes, P;
   size_t smem;
 };
-constexpr int kGatherSlotBudget = 3584;
-constexpr size_t kGatherSmemBudget = 220 * 1024;
-GatherGeom gather_geom(int row1, int d, int k1, int k, bool rerank);
+constexpr int kGatherSlotBudget = 13312;
+constexpr size_t kGatherSmemBudget = 226 * 1024;
+GatherGeom gather_geom(int row1, int d, int k);
 cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
-                          const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
-                          float* out_scores, cudaStream_t stream);
+                          const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
+                          cudaStream_t stream);
 
 }  // namespace lvq

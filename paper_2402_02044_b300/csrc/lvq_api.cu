@@ -642,6 +642,10 @@ lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq
   c0.take<float>(nq);
   c0.take<float>(nq);
   c0.take<float>((size_t)nq * st.n_means);
+  if (two) {
+    c0.take<int64_t>((size_t)nq * k1);
+    c0.take<float>((size_t)nq * k1);
+  }
   rc = ensure_ws(s, c0.off);
   if (rc != LVQ_OK) return rc;
   Carver c(s->ws);
@@ -658,8 +662,21 @@ lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq
     Prof pr(s, str, LVQ_K_PREP);
     LVQ_CUDA(s, launch_prep_queries(st, q, nq, p, str), "prep_queries");
   }
-  Prof pg(s, str, LVQ_K_GATHER);
-  LVQ_CUDA(s, launch_gather(st, q, nq, p, cand, n_cand, two ? k1 : k, k, two, out_ids, out_scores, str), "gather");
+  if (!two) {
+    Prof pg(s, str, LVQ_K_GATHER);
+    LVQ_CUDA(s, launch_gather(st, q, nq, p, cand, n_cand, k, out_ids, out_scores, str), "gather");
+    return LVQ_OK;
+  }
+  // first level: the k1 best distinct candidates per query; then both levels
+  // re-rank them, every query's candidates in flight at once
+  int64_t* ids1 = c.take<int64_t>((size_t)nq * k1);
+  float* sc1 = c.take<float>((size_t)nq * k1);
+  {
+    Prof pg(s, str, LVQ_K_GATHER);
+    LVQ_CUDA(s, launch_gather(st, q, nq, p, cand, n_cand, k1, ids1, sc1, str), "gather");
+  }
+  Prof pr(s, str, LVQ_K_RERANK);
+  LVQ_CUDA(s, launch_rerank(st, q, nq, p, ids1, k1, k, out_ids, out_scores, str), "rerank");
   return LVQ_OK;
 }
 

@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
 // cp.async copies (one commit group per batch; the lanes of a warp copy
 // consecutive chunks of a row, so every row is read with coalesced requests),
 // issuing P - 1 batches ahead of the one it scores, across query boundaries
-// too, so the next query's first rows load while the block selects and
-// re-ranks.  A row is scored by L lanes (16-byte chunks l, l + L, ...); the
+// too, so the next query's first rows load while the block selects the
+// query's best keys.  A row is scored by L lanes (16-byte chunks l, l + L, ...); the
 // slot stride makes the lanes of a quarter warp hit distinct banks.
 // Products: <q, c> is computed exactly in integers: the query is rounded once
 // to 24-bit fixed point (Q_j = rint(q_j / s), s = max|q| / (2^23 - 1)), Q is
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float
 // offset and scaled by s once per candidate.  Rounding q moves a score by at
 // most (s / 2) sqrt(d) ||x^|| <= 6e-8 sqrt(d) ||q|| ||x^||, a small fraction of
 // the float32 tolerance.
-constexpr int kGatherThreads = 256;
+constexpr int kGatherThreads = 128;
 constexpr int kGW = kGatherThreads / 32;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // an empty row of a batch
 
@@ -360,23 +360,19 @@ __device__ __forceinline__ void group4(GatherAcc& A, uint32_t w, uint2 p0, uint2
 
 __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore st, const float* __restrict__ q,
                                                                  int64_t nq, QueryPrep p,
-                                                                 const int64_t* __restrict__ cand, int n_cand, int k1,
-                                                                 int k, int rerank, GatherGeom gg, int64_t* out_ids,
+                                                                 const int64_t* __restrict__ cand, int n_cand,
+                                                                 int k, GatherGeom gg, int64_t* out_ids,
                                                                  float* out_scores) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int d = st.d;
   const int groups = (d + 7) >> 3, gpad = (groups + 3) & ~3;
-  const int stage1 = rerank ? k1 : k;
-  const int cap = pow2_at_least(stage1 + kGatherThreads);
+  const int cap = pow2_at_least(k + 2 * kGatherThreads);  // cuts are rare once the bound is set
   const int R = gg.R, L = 32 / gg.R, P = gg.P;
   unsigned char* slots = smem;  // [kGW][P][slot_bytes]
   uint32_t* slot_ids = reinterpret_cast<uint32_t*>(slots + (size_t)kGW * P * gg.slot_bytes);  // [kGW][P][32]
   uint2* planes = reinterpret_cast<uint2*>(slot_ids + kGW * P * 32);                       // [3][gpad]
-  float* qsh = reinterpret_cast<float*>(planes + 3 * gpad);                                // [groups * 8]
-  uint64_t* buf = reinterpret_cast<uint64_t*>(qsh + groups * 8);                          // [cap]
-  uint64_t* tmp = buf + cap;                                                                // [cap]
-  uint64_t* scratch = tmp + cap;                        // [pow2_at_least(stage1)]
-  int* sh_pos = reinterpret_cast<int*>(scratch + pow2_at_least(stage1));  // [k + 2]
+  uint64_t* buf = reinterpret_cast<uint64_t*>(planes + 3 * gpad);                         // [cap]
+  int* sh_pos = reinterpret_cast<int*>(buf + cap);                                          // [k + 2]
   __shared__ int cnt;
   __shared__ uint64_t thr;
   __shared__ int scan_sh[kGW + 1];
@@ -463,7 +459,6 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     float mx = 0.0f;
     for (int j = threadIdx.x; j < groups * 8; j += blockDim.x) {
       const float v = j < d ? qrow[j] : 0.0f;
-      qsh[j] = v;
       mx = fmaxf(mx, fabsf(v));
     }
 #pragma unroll
@@ -490,7 +485,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int j = 8 * g + plane_dim(st.bits1, h, b);
-            const int v = j < d ? max(-8388607, min(8388607, __float2int_rn(qsh[j] * qinv))) : 0;
+            const int v = j < d ? max(-8388607, min(8388607, __float2int_rn(qrow[j] * qinv))) : 0;
             part += v;
             pw[0][h] |= (uint32_t)(v & 255) << (8 * b);
             pw[1][h] |= (uint32_t)((v >> 8) & 255) << (8 * b);
@@ -568,7 +563,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
       __syncthreads();
       if (cnt > cap - kGatherThreads) {
         uint64_t t;
-        const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
+        const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
         if (threadIdx.x == 0) {
           cnt = kept;
           thr = t;
@@ -578,16 +573,13 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     }
     {
       uint64_t t;
-      const int kept = block_select_dedupe(buf, tmp, cap, cnt, stage1, scan_sh, &t);
+      const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
       if (threadIdx.x == 0) cnt = kept;
       __syncthreads();
     }
     int64_t* oi = out_ids + qi * k;
     float* os = out_scores + qi * k;
-    if (!rerank)
-      write_results(buf, cnt, k, st.metric, oi, os, sh_pos);
-    else
-      rerank_tail(st, qsh, buf, cnt, k, scratch, sh_pos, oi, os);
+    write_results(buf, cnt, k, st.metric, oi, os, sh_pos);
   }
   cp_async_wait<0>();
 }
@@ -648,34 +640,41 @@ cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, con
   return cudaGetLastError();
 }
 
-GatherGeom gather_geom(int row1, int d, int k1, int k, bool rerank) {
-  GatherGeom g{};
+GatherGeom gather_geom(int row1, int d, int k) {
+  // The widest batches (fewest per-batch steps per row) with three slots per
+  // warp, else two, that let two blocks share an SM (one block's select and
+  // re-rank then overlap the other's streaming); failing that, the widest that
+  // fit at all.  Each batch holds at most kGatherSlotBudget bytes.
   const int r16 = row1 / 16;
-  for (int R = 32; R >= 1; R >>= 1) {
-    const int L = 32 / R;
-    int s16 = r16;
-    if (L < 8)
-      while (s16 % (2 * L) != L) ++s16;  // the rows of a quarter warp start in distinct banks
-    g.R = R;
-    g.stride = s16 * 16;
-    g.slot_bytes = R * g.stride;
-    if (g.slot_bytes <= kGatherSlotBudget) break;
-  }
-  const int stage1 = rerank ? k1 : k;
   const int groups = (d + 7) / 8, gpad = (groups + 3) & ~3;
-  const size_t rest = (size_t)(2 * pow2_at_least(stage1 + kGatherThreads) + pow2_at_least(stage1)) * 8 +
-                      (size_t)gpad * 3 * 8 + (size_t)groups * 8 * 4 + (size_t)(k + 2) * 4 + 16;
-  for (g.P = 3; g.P > 2; --g.P)
-    if ((size_t)kGW * g.P * (g.slot_bytes + 32 * 4) + rest <= kGatherSmemBudget) break;
-  g.smem = (size_t)kGW * g.P * (g.slot_bytes + 32 * 4) + rest;
-  return g;
+  (void)groups;
+  const size_t rest = (size_t)pow2_at_least(k + 2 * kGatherThreads) * 8 + (size_t)gpad * 3 * 8 + (size_t)(k + 2) * 4 + 16;
+  GatherGeom g{};
+  for (const size_t budget : {kGatherSmemBudget / 2 - 1024, kGatherSmemBudget}) {
+    for (int R = 32; R >= 1; R >>= 1) {
+      if (budget < kGatherSmemBudget && R < 8) break;
+      const int L = 32 / R;
+      int s16 = r16;
+      if (L < 8)
+        while (s16 % (2 * L) != L) ++s16;  // the rows of a quarter warp start in distinct banks
+      g.R = R;
+      g.stride = s16 * 16;
+      g.slot_bytes = R * g.stride;
+      if (g.slot_bytes > kGatherSlotBudget && R > 1) continue;
+      for (g.P = 3; g.P >= 2; --g.P) {
+        g.smem = (size_t)kGW * g.P * (g.slot_bytes + 32 * 4) + rest;
+        if (g.smem <= budget) return g;
+      }
+    }
+  }
+  return g;  // does not fit: the launcher refuses it
 }
 
 cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
-                          const int64_t* cand, int n_cand, int k1, int k, bool rerank, int64_t* out_ids,
-                          float* out_scores, cudaStream_t stream) {
+                          const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
+                          cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
-  const GatherGeom g = gather_geom(st.row1, st.d, k1, k, rerank);
+  const GatherGeom g = gather_geom(st.row1, st.d, k);
   if (g.smem > kGatherSmemBudget) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
@@ -690,8 +689,8 @@ cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, con
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_kernel, kGatherThreads, g.smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t grid = std::min<int64_t>(nq, (int64_t)sms * per_sm);
-  gather_kernel<<<(unsigned)grid, kGatherThreads, g.smem, stream>>>(st, q, nq, p, cand, n_cand, k1, k,
-                                                                   rerank ? 1 : 0, g, out_ids, out_scores);
+  gather_kernel<<<(unsigned)grid, kGatherThreads, g.smem, stream>>>(st, q, nq, p, cand, n_cand, k, g, out_ids,
+                                                                   out_scores);
   return cudaGetLastError();
 }
 

@@ -589,29 +589,32 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) 
   return before;
 }
 
-// Block-wide: sort buf[0..cap) (entries from n on are overwritten with
-// kNoKey), drop repeated keys, keep the k best at buf[0..kept) in ascending
-// order.  tmp: cap keys of shared memory; sh: blockDim/32 + 1 ints.
-// Returns kept; *thr = k-th best key if k were kept, else kNoKey.
-__device__ __forceinline__ int block_select_dedupe(uint64_t* buf, uint64_t* tmp, int cap, int n, int k, int* sh,
-                                                   uint64_t* thr) {
+// Cut buf[0..n) (n <= cap, cap a power of two) to its k best distinct keys,
+// sorted, in place; returns how many were kept and sets *thr to the k-th key
+// (kNoKey if fewer than k).  Called by all threads; sh: blockDim/32 + 1 ints.
+// Each chunk of the sorted keys is read before any survivor of it is written
+// (survivors only move down), so the compaction needs no second buffer.
+__device__ __forceinline__ int block_select_dedupe(uint64_t* buf, int cap, int n, int k, int* sh, uint64_t* thr) {
   for (int i = n + threadIdx.x; i < cap; i += blockDim.x) buf[i] = kNoKey;
   block_sort(buf, cap);
   int written = 0;
-  for (int base = 0; base < cap; base += blockDim.x) {
+  uint64_t prev_last = kNoKey;  // the previous chunk's last key, read before it was overwritten
+  for (int base = 0; base < cap && written < k; base += blockDim.x) {
     const int i = base + threadIdx.x;
     const uint64_t key = i < cap ? buf[i] : kNoKey;
-    const bool keep = i < cap && key != kNoKey && (i == 0 || key != buf[i - 1]);
+    const uint64_t prev = threadIdx.x == 0 ? prev_last : (i < cap ? buf[i - 1] : kNoKey);
+    const uint64_t last = buf[(base + (int)blockDim.x < cap ? base + (int)blockDim.x : cap) - 1];
+    const bool keep = i < cap && key != kNoKey && key != prev;
+    prev_last = last;
     int total;
-    const int pos = written + block_exclusive_scan(keep ? 1 : 0, sh, total);
-    if (keep) tmp[pos] = key;
+    const int pos = written + block_exclusive_scan(keep ? 1 : 0, sh, total);  // ends with a barrier
+    if (keep && pos < k) buf[pos] = key;
     written += total;
+    __syncthreads();
   }
-  __syncthreads();
   const int kept = written < k ? written : k;
-  for (int i = threadIdx.x; i < kept; i += blockDim.x) buf[i] = tmp[i];
-  __syncthreads();
   *thr = (kept == k && k > 0) ? buf[k - 1] : kNoKey;
+  __syncthreads();
   return kept;
 }
 
