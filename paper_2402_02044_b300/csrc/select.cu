@@ -522,35 +522,59 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
           c_slot = c_slot + 1 == P ? 0 : c_slot + 1;
           ++c_n;
           load_consts(c_n, c_slot);
-          GatherAcc A{0u, 0u, 0};
+          // four accumulator sets (one per code group of a chunk, two chunks at
+          // a time) keep the dp4a dependence chains short
+          GatherAcc A[4] = {{0u, 0u, 0}, {0u, 0u, 0}, {0u, 0u, 0}, {0u, 0u, 0}};
           if (su != kNoSlot) {
             const uint4* row = reinterpret_cast<const uint4*>(slots + (size_t)(w * P + slot) * gg.slot_bytes +
                                                               (size_t)r * gg.stride);
-            for (int c = l; c < nchunks; c += L) {
-              const uint4 cw = row[c];
+            auto chunk4 = [&](const uint4 cw, int c) {
+              const uint4 a0 = pl4[2 * c], a1 = pl4[2 * c + 1];
+              const uint4 b0 = pl4[pstride4 + 2 * c], b1 = pl4[pstride4 + 2 * c + 1];
+              const uint4 c0 = pl4[2 * pstride4 + 2 * c], c1 = pl4[2 * pstride4 + 2 * c + 1];
+              group4(A[0], cw.x, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
+              group4(A[1], cw.y, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
+              group4(A[2], cw.z, make_uint2(a1.x, a1.y), make_uint2(b1.x, b1.y), make_uint2(c1.x, c1.y));
+              group4(A[3], cw.w, make_uint2(a1.z, a1.w), make_uint2(b1.z, b1.w), make_uint2(c1.z, c1.w));
+            };
+            auto chunk8 = [&](const uint4 cw, int c, int h) {
+              const uint4 a0 = pl4[c], b0 = pl4[pstride4 + c], c0 = pl4[2 * pstride4 + c];
+              plane_step(A[2 * h], cw.x, cw.y, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
+              plane_step(A[2 * h + 1], cw.z, cw.w, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w),
+                         make_uint2(c0.z, c0.w));
+            };
+            int c = l;
+            for (; c + L < nchunks; c += 2 * L) {
+              const uint4 cw0 = row[c], cw1 = row[c + L];
               if (b4) {
-                const uint4 a0 = pl4[2 * c], a1 = pl4[2 * c + 1];
-                const uint4 b0 = pl4[pstride4 + 2 * c], b1 = pl4[pstride4 + 2 * c + 1];
-                const uint4 c0 = pl4[2 * pstride4 + 2 * c], c1 = pl4[2 * pstride4 + 2 * c + 1];
-                group4(A, cw.x, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
-                group4(A, cw.y, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
-                group4(A, cw.z, make_uint2(a1.x, a1.y), make_uint2(b1.x, b1.y), make_uint2(c1.x, c1.y));
-                group4(A, cw.w, make_uint2(a1.z, a1.w), make_uint2(b1.z, b1.w), make_uint2(c1.z, c1.w));
+                chunk4(cw0, c);
+                chunk4(cw1, c + L);
               } else {
-                const uint4 a0 = pl4[c], b0 = pl4[pstride4 + c], c0 = pl4[2 * pstride4 + c];
-                plane_step(A, cw.x, cw.y, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
-                plane_step(A, cw.z, cw.w, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
+                chunk8(cw0, c, 0);
+                chunk8(cw1, c + L, 1);
               }
+            }
+            if (c < nchunks) {
+              if (b4)
+                chunk4(row[c], c);
+              else
+                chunk8(row[c], c, 0);
+            }
+#pragma unroll
+            for (int i = 1; i < 4; ++i) {
+              A[0].a0 += A[i].a0;
+              A[0].a1 += A[i].a1;
+              A[0].a2 += A[i].a2;
             }
           }
           // the L lanes of a row are consecutive
           for (int o = L >> 1; o > 0; o >>= 1) {
-            A.a0 += __shfl_xor_sync(kFull, A.a0, o);
-            A.a1 += __shfl_xor_sync(kFull, A.a1, o);
-            A.a2 += __shfl_xor_sync(kFull, A.a2, o);
+            A[0].a0 += __shfl_xor_sync(kFull, A[0].a0, o);
+            A[0].a1 += __shfl_xor_sync(kFull, A[0].a1, o);
+            A[0].a2 += __shfl_xor_sync(kFull, A[0].a2, o);
           }
           if (l == 0 && live) {
-            const long long dot = (long long)A.a0 + ((long long)A.a1 << 8) + ((long long)A.a2 << 16) - qoff;
+            const long long dot = (long long)A[0].a0 + ((long long)A[0].a1 << 8) + ((long long)A[0].a2 << 16) - qoff;
             const float a = __fmul_rn(qscale, (float)dot);
             float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo), qs, cmq[m]));
             if (!ip) sc = __fadd_rn(__fadd_rn(qn, nrm), -2.0f * sc);
