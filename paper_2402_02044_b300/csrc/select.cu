@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) prep_kernel(DeviceStore st, const float* 
 // writes the k best.  With a single centring mean the mean is folded into the
 // query first: q - mu for L2 (qsh is overwritten), <q, mu> added once for the
 // inner product.  scratch: pow2_at_least(n) keys of shared memory.
-constexpr int kRU = 4;
+constexpr int kRU = 2;
 constexpr int kRG = 3;
 
 __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* keys, int n, int k, uint64_t* scratch,
@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const f
 }
 
 // ---- re-rank of caller-given candidates (one block per query) -----------------
-__global__ void __launch_bounds__(256) rerank_kernel(DeviceStore st, const float* __restrict__ q,
+constexpr int kRerankThreads = 128;
+
+__global__ void __launch_bounds__(kRerankThreads, 8) rerank_kernel(DeviceStore st, const float* __restrict__ q,
                                                       const int64_t* __restrict__ ids, int k1, int k,
                                                       int64_t* out_ids, float* out_scores) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -660,7 +662,7 @@ cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, con
     cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  rerank_kernel<<<(unsigned)nq, 256, sm, stream>>>(st, q, ids, k1, k, out_ids, out_scores);
+  rerank_kernel<<<(unsigned)nq, kRerankThreads, sm, stream>>>(st, q, ids, k1, k, out_ids, out_scores);
   return cudaGetLastError();
 }
 
