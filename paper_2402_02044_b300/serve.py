@@ -149,7 +149,7 @@ class _Lane:
 class Server:
     def __init__(self, store: Store, lanes: int = 2, max_batch: int = 4096, k1: int = 100, kmax: int = 100,
                  precision: str = "auto", hbm_budget: Optional[int] = None, use_graphs: bool = False,
-                 tuning: Optional[dict] = None):
+                 tuning: Optional[dict] = None, warmup: bool = True):
         self.store = store
         self.d = store.d
         self.k1 = k1 if store.bits2 else 0
@@ -163,6 +163,8 @@ class Server:
             hbm_budget = free // 2
         self.admission = Admission(hbm_budget)
         self.lanes = [_Lane(store, self.d, max_batch, kmax, max(self.k1, kmax)) for _ in range(lanes)]
+        if warmup:
+            self._warmup()
         self.upd_stream = torch.cuda.Stream()
         self.pending_q = collections.deque()
         self.pending_upd = collections.deque()
@@ -178,6 +180,19 @@ class Server:
         self._stop = False
         self._thread = threading.Thread(target=self._run, name="lvq-serve", daemon=True)
         self._thread.start()
+
+    def _warmup(self):
+        """One search per lane at each batch size that selects a different
+        kernel (integer scan for 1, 2 and 3-4 queries; tensor-core tiles of
+        16, 32, 64 and 128 queries; the merge for fewer or more queries than
+        SMs), so that first-use costs (module loading, kernel attributes,
+        scratch) are paid before the first request rather than by it."""
+        for lane in self.lanes:
+            for nb in (1, 2, 4, 16, 32, 64, 128, 256):
+                if nb <= self.max_batch:
+                    with torch.cuda.stream(lane.stream):
+                        self._search(lane, nb, self.kmax)
+            lane.stream.synchronize()
 
     # ------------------------------------------------------------ client API
     def submit_query(self, q: np.ndarray, k: int) -> Future:
