@@ -252,6 +252,47 @@ def test_candidates_widths_dims_means(case):
     st.close()
 
 
+def test_candidates_many_queries_per_block_and_limits():
+    """More queries than resident gather blocks (each block walks several
+    queries, its row ring running across query boundaries), the largest k1,
+    a single candidate, the longest candidate list, and lists that are all
+    skipped or all deleted."""
+    n, d = 6000, 768
+    x, q, means = gmm_case(n, d, 16, "ip", 700, seed=77)
+    st, ids = lib_store(x, means, 4, 8, "ip")
+    enc = O.encode(x, means, 4, 8)
+    g = np.random.default_rng(12)
+    qt = torch.from_numpy(q).cuda()
+    # 700 queries x 90 candidates: several queries per block
+    cand = g.integers(0, n, (700, 90)).astype(np.int64)
+    gi, gs = st.search_candidates(qt, torch.from_numpy(cand).cuda(), 10, 0)
+    check_scores(q, gi, gs, enc, means, "ip", 1, TOL_FP32)
+    check_topk_ids(q, gi, enc, means, "ip", 10, TOL_FP32, cand_ids=cand)
+    # the largest k1 (512) over 3000 candidates, re-ranked
+    c2 = g.integers(0, n, (3, 3000)).astype(np.int64)
+    gi, gs = st.search_candidates(qt[:3], torch.from_numpy(c2).cuda(), 20, 512)
+    check_scores(q[:3], gi, gs, enc, means, "ip", 2, TOL_FP32)
+    check_two_level(q[:3], gi, enc, means, "ip", 512, 20, TOL_FP32, cand_ids=c2)
+    # one candidate; the longest list (every id, many times over)
+    c3 = g.integers(0, n, (2, 1)).astype(np.int64)
+    gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c3).cuda(), 5, 0)
+    gi = gi.cpu().numpy()
+    assert (gi[:, 0] == c3[:, 0]).all() and (gi[:, 1:] == -1).all()
+    c4 = np.tile(np.arange(65536, dtype=np.int64) % n, (2, 1))
+    gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c4).cuda(), 10, 0)
+    check_topk_ids(q[:2], gi, enc, means, "ip", 10, TOL_FP32)
+    # all skipped / all deleted
+    c5 = np.full((2, 40), -1, dtype=np.int64)
+    gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c5).cuda(), 5, 10)
+    assert (gi.cpu().numpy() == -1).all()
+    c6 = g.integers(0, n, (2, 40)).astype(np.int64)
+    st.delete(torch.from_numpy(np.unique(c6)).cuda())
+    gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c6).cuda(), 5, 0)
+    assert (gi.cpu().numpy() == -1).all()
+    check_no_device_error(st)
+    st.close()
+
+
 def test_streaming_slots_match_the_replay():
     d, cap = 40, 5000
     mix = synth.Mixture(d=d, n_comp=8, sigma=0.3, seed=3)
