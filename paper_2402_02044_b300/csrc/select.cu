@@ -667,18 +667,21 @@ cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, con
 }
 
 GatherGeom gather_geom(int row1, int d, int k) {
-  // The widest batches (fewest per-batch steps per row) with three slots per
-  // warp, else two, that let two blocks share an SM (one block's select and
-  // re-rank then overlap the other's streaming); failing that, the widest that
-  // fit at all.  Each batch holds at most kGatherSlotBudget bytes.
+  // The widest batches (fewest per-batch steps per row, at least 16 rows)
+  // with three slots per warp, else two, that let three blocks share an SM,
+  // else two (more warps to issue while others wait on their rings; one
+  // block's select overlaps the others' streaming); failing that, the widest
+  // that fit at all.  Each batch holds at most kGatherSlotBudget bytes.
+  // Measured at d = 768, 4-bit, 1,024 x 2,048 ids: 3 blocks x 16-row batches
+  // 0.43 ms, 2 blocks x 32 rows 0.49 ms, 4 blocks x 8 rows 0.63 ms.
   const int r16 = row1 / 16;
   const int groups = (d + 7) / 8, gpad = (groups + 3) & ~3;
   (void)groups;
   const size_t rest = (size_t)pow2_at_least(k + 2 * kGatherThreads) * 8 + (size_t)gpad * 3 * 8 + (size_t)(k + 2) * 4 + 16;
   GatherGeom g{};
-  for (const size_t budget : {kGatherSmemBudget / 2 - 1024, kGatherSmemBudget}) {
+  for (const size_t budget : {kGatherSmemBudget / 3 - 1024, kGatherSmemBudget / 2 - 1024, kGatherSmemBudget}) {
     for (int R = 32; R >= 1; R >>= 1) {
-      if (budget < kGatherSmemBudget && R < 8) break;
+      if (budget < kGatherSmemBudget && R < 16) break;
       const int L = 32 / R;
       int s16 = r16;
       if (L < 8)
