@@ -10,15 +10,21 @@ Model
   sizes) and run on one of several *lanes*: a store view (own scratch
   memory) with its own CUDA stream, so batches overlap on the device.  A
   request's rows are re-split from the batch's results (the top-k of a query
-  is the first k of its top-k_max list).
+  is the first k of its top-k_max list).  A request of more than max_batch
+  rows is cut into parts of at most max_batch rows that queue one after
+  another; its future completes when the last part does.  Beyond one or two
+  query tiles a batch gains no throughput (the scan's cost grows with its
+  rows), so a small max_batch bounds how long a request waits behind others.
 * Insert requests are encoded at once on an update stream with
   ``lvq_insert_deferred``: their slots are written while searches run, but
   stay invisible.  Deletes are queued.
 * Visibility changes at *epoch* boundaries: when updates are pending, the
   scheduler stops starting new query batches, waits for the ones in flight,
-  publishes the pending inserts and applies the deletes, then resumes.  Every
-  query therefore sees exactly the store state of the epoch it ran in, and a
-  request's result is the same whether it ran alone or batched with others.
+  publishes the pending inserts and applies the deletes, then resumes; the
+  remaining parts of a request already started are launched first, so all
+  parts of a request run in one epoch.  Every query therefore sees exactly
+  the store state of the epoch it ran in, and a request's result is the same
+  whether it ran alone, split or batched with others.
 * Admission: each request holds device bytes (its inputs and outputs) while
   in flight; a request waits while the total would exceed the HBM budget,
   and one that could never fit is rejected.
@@ -51,6 +57,20 @@ class Request:
     t_submit: float = 0.0
     nbytes: int = 0
     epoch: int = -1
+    group: Optional["_Group"] = None  # the request this one is a part of
+    part: int = 0
+
+
+class _Group:
+    """A query request cut into parts: results are gathered in part order."""
+
+    def __init__(self, parts: int, future: Future, rows: int):
+        self.results = [None] * parts
+        self.remaining = parts
+        self.launched = 0
+        self.future = future
+        self.rows = rows
+        self.epoch = -1
 
 
 def request_bytes(kind: str, n: int, d: int, k: int) -> int:
@@ -83,12 +103,15 @@ class Admission:
         assert self.used >= 0
 
 
-def form_batch(pending: "collections.deque[Request]", max_batch: int, admission: Admission):
+def form_batch(pending: "collections.deque[Request]", max_batch: int, admission: Admission, accept=None):
     """Take query requests from the head of the queue, in order, while the
-    batch stays within max_batch rows and the admission budget."""
+    batch stays within max_batch rows and the admission budget (and, when
+    given, while accept(request) holds)."""
     batch, rows = [], 0
     while pending:
         r = pending[0]
+        if accept is not None and not accept(r):
+            break
         n = r.data.shape[0]
         if batch and rows + n > max_batch:
             break
@@ -173,6 +196,7 @@ class Server:
         self.inflight_upd = []    # (event, request, result tensor, kind)
         self.epoch = 0
         self.epoch_event = None
+        self.open_groups = set()  # split requests with some but not all parts launched
         self.stats = LatencyStats()
         self.rejected = 0
         self._lock = threading.Lock()
@@ -197,9 +221,25 @@ class Server:
     # ------------------------------------------------------------ client API
     def submit_query(self, q: np.ndarray, k: int) -> Future:
         q = np.ascontiguousarray(q, dtype=np.float32).reshape(-1, self.d)
-        if not 1 <= k <= self.kmax or q.shape[0] > self.max_batch:
+        if not 1 <= k <= self.kmax or q.shape[0] < 1:
             raise ValueError("k or batch size out of range")
-        return self._submit(Request(QUERY, q, k, nbytes=request_bytes(QUERY, len(q), self.d, k)))
+        if q.shape[0] <= self.max_batch:
+            return self._submit(Request(QUERY, q, k, nbytes=request_bytes(QUERY, len(q), self.d, k)))
+        fut = Future()
+        cuts = list(range(0, q.shape[0], self.max_batch))
+        grp = _Group(len(cuts), fut, q.shape[0])
+        t = time.perf_counter()
+        parts = [Request(QUERY, q[a:a + self.max_batch], k, t_submit=t, group=grp, part=i,
+                         nbytes=request_bytes(QUERY, len(q[a:a + self.max_batch]), self.d, k))
+                 for i, a in enumerate(cuts)]
+        with self._lock:
+            if any(not self.admission.fits_ever(r.nbytes) for r in parts):
+                self.rejected += 1
+                fut.set_exception(MemoryError("request larger than the HBM budget"))
+                return fut
+            self.pending_q.extend(parts)
+            self._wake.notify_all()
+        return fut
 
     def submit_insert(self, x: np.ndarray) -> Future:
         x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.d)
@@ -268,11 +308,15 @@ class Server:
         progressed = self._complete()
         progressed |= self._stage_updates()
         updates_waiting = bool(self.staged or self.deletes)
-        if updates_waiting and all(l.busy is None for l in self.lanes) and not self.inflight_upd:
+        if (updates_waiting and not self.open_groups and all(l.busy is None for l in self.lanes)
+                and not self.inflight_upd):
             self._epoch_boundary()
             progressed = True
         elif not updates_waiting:
             progressed |= self._launch_queries()
+        elif self.open_groups:
+            # the rest of a split request runs in the epoch its first part ran in
+            progressed |= self._launch_queries(only_open=True)
         return progressed
 
     def _complete(self) -> bool:
@@ -289,10 +333,20 @@ class Server:
             with self._lock:
                 for r in batch:
                     n = r.data.shape[0]
-                    r.future.set_result((ids[off:off + n, :r.k].copy(), sc[off:off + n, :r.k].copy(), r.epoch))
+                    res = (ids[off:off + n, :r.k].copy(), sc[off:off + n, :r.k].copy())
                     off += n
                     self.admission.give(r.nbytes)
-                    self.stats.add(r.t_submit, t, n)
+                    g = r.group
+                    if g is None:
+                        r.future.set_result(res + (r.epoch,))
+                        self.stats.add(r.t_submit, t, n)
+                        continue
+                    g.results[r.part] = res
+                    g.remaining -= 1
+                    if g.remaining == 0:
+                        g.future.set_result((np.concatenate([a for a, _ in g.results]),
+                                             np.concatenate([b for _, b in g.results]), g.epoch))
+                        self.stats.add(r.t_submit, t, g.rows)
             done_any = True
         keep = []
         for item in self.inflight_upd:
@@ -349,19 +403,28 @@ class Server:
         self.epoch_event = ev
         self.epoch += 1
 
-    def _launch_queries(self) -> bool:
+    def _launch_queries(self, only_open: bool = False) -> bool:
         launched = False
+        accept = (lambda r: r.group is not None and r.group in self.open_groups) if only_open else None
         for lane in self.lanes:
             if lane.busy is not None:
                 continue
             with self._lock:
-                batch = form_batch(self.pending_q, self.max_batch, self.admission)
+                batch = form_batch(self.pending_q, self.max_batch, self.admission, accept)
             if not batch:
                 break
             rows = sum(r.data.shape[0] for r in batch)
             kb = max(r.k for r in batch)
             for r in batch:
                 r.epoch = self.epoch
+                g = r.group
+                if g is not None:
+                    g.epoch = self.epoch
+                    g.launched += 1
+                    if g.launched < len(g.results):
+                        self.open_groups.add(g)
+                    else:
+                        self.open_groups.discard(g)
             self._run_batch(lane, batch, rows, kb)
             launched = True
         return launched

@@ -59,6 +59,33 @@ def test_results_alone_equal_results_in_the_mix(graphs):
     st.close()
 
 
+def test_requests_larger_than_a_batch_are_split_within_one_epoch():
+    """A request of more rows than max_batch runs as parts of at most
+    max_batch rows; its result equals the direct search, and updates
+    submitted while it runs apply to all of its parts or to none."""
+    from paper_2402_02044_b300.serve import Server
+    mix, x, means, st = _setup(n=20000)
+    srv = Server(st, lanes=2, max_batch=64, k1=50, kmax=10, precision="fp16")
+    qs = [mix.rows(2000 * i, 2000 * i + n, stream=21) for i, n in enumerate([1, 200, 65, 130, 7])]
+    res = [srv.submit_query(q, 10).result(timeout=60) for q in qs]
+    for q, (ri, rs, _) in zip(qs, res):
+        assert ri.shape == (len(q), 10)
+        di, ds = st.search(torch.from_numpy(q).cuda(), 10, 50, "fp16")
+        assert np.array_equal(di.cpu().numpy(), ri) and np.array_equal(ds.cpu().numpy(), rs)
+    # a 400-row request (7 parts) with a delete of its current best answers behind it
+    big = mix.rows(50000, 50400, stream=22)
+    before = st.search(torch.from_numpy(big).cuda(), 10, 50, "fp16")[0].cpu().numpy()
+    fq = srv.submit_query(big, 10)
+    fd = srv.submit_delete(np.unique(before[:, 0]))
+    gi, gs, ep = fq.result(timeout=60)
+    fd.result(timeout=60)
+    srv.drain()
+    after = st.search(torch.from_numpy(big).cuda(), 10, 50, "fp16")[0].cpu().numpy()
+    assert np.array_equal(gi, before) or np.array_equal(gi, after)
+    srv.close()
+    st.close()
+
+
 def test_updates_become_visible_at_epoch_boundaries():
     from paper_2402_02044_b300.serve import Server
     mix, x, means, st = _setup(n=20000, d=64, metric="l2")

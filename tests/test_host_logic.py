@@ -37,6 +37,15 @@ def test_form_batch_keeps_order_and_limits():
     assert [r.data.shape[0] for r in form_batch(q, 10, a)] == [40]
 
 
+def test_form_batch_takes_only_accepted_heads():
+    q = collections.deque([_req(3), _req(5), _req(2)])
+    q[0].group = q[1].group = "open"
+    a = Admission(10 ** 9)
+    b = form_batch(q, 100, a, accept=lambda r: r.group == "open")
+    assert [r.data.shape[0] for r in b] == [3, 5] and [r.data.shape[0] for r in q] == [2]
+    assert form_batch(q, 100, a, accept=lambda r: r.group == "open") == []
+
+
 def test_form_batch_respects_the_byte_budget():
     one = request_bytes(QUERY, 4, 8, 10)
     a = Admission(2 * one + 1)
