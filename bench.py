@@ -194,7 +194,11 @@ def serve_leg(st, mix, n, avoid, duration_s=6.0, rate=40.0, update_every_s=0.25,
     n_upd = int(t_arr[-1] / update_every_s) + 1
     cand = synth.choose(n, min(n, 3 * n_upd * B_upd), seed + 4)
     cand = cand[~np.isin(cand, np.fromiter(avoid, dtype=np.int64, count=len(avoid)))][:n_upd * B_upd]
-    srv = Server(st, lanes=2, max_batch=4096, k1=100, kmax=100, precision="auto")
+    # every update batch is generated before the trace starts, so that the
+    # client thread does no heavy work (and holds no interpreter lock) while
+    # requests are in flight
+    upd_rows = [mix.rows(u * B_upd, (u + 1) * B_upd, stream=13) for u in range(n_upd)]
+    srv = Server(st, lanes=2, max_batch=1024, k1=100, kmax=100, precision="auto")
     futs, upd = [], []
     t0 = time.perf_counter()
     next_upd, u = 0.0, 0
@@ -203,7 +207,7 @@ def serve_leg(st, mix, n, avoid, duration_s=6.0, rate=40.0, update_every_s=0.25,
             now = time.perf_counter() - t0
             if u < n_upd and now >= next_upd and (u + 1) * B_upd <= len(cand):
                 upd.append(srv.submit_delete(cand[u * B_upd:(u + 1) * B_upd]))
-                upd.append(srv.submit_insert(mix.rows(u * B_upd, (u + 1) * B_upd, stream=13)))
+                upd.append(srv.submit_insert(upd_rows[u]))
                 u += 1
                 next_upd += update_every_s
             if now >= t_arr[i]:
@@ -225,7 +229,8 @@ def serve_leg(st, mix, n, avoid, duration_s=6.0, rate=40.0, update_every_s=0.25,
             "mean_ms": s.get("mean_ms"), "qps": s.get("qps"), "epochs": s.get("epochs"),
             "offered": f"{rate:g} query batches/s (Poisson, sizes log-uniform 1..4096, k in {{10, 100}}) for "
                        f"{duration_s:g} s; every {update_every_s:g} s insert {B_upd} + delete {B_upd}",
-            "update_batches": 2 * u, "update_failures": failed, "lanes": 2, "precision": "auto"}
+            "update_batches": 2 * u, "update_failures": failed, "lanes": 2, "max_batch": 1024,
+            "precision": "auto"}
 
 
 def recall_sample(mix, means, q_host, precisions, n_rows=100_000, n_queries=8, k1=100, k=10):

@@ -150,6 +150,38 @@ lvq_status lvq_publish(lvq_store *store, const int64_t *ids, int64_t n, lvq_stre
 lvq_status lvq_delete(lvq_store *store, const int64_t *ids, int64_t n, int64_t *out_n_deleted,
                       lvq_stream_t stream);
 
+/* Delete and hold (Sec. 2.1, lazy deletion of App. A.2): like lvq_delete,
+ * but a slot that was live also stays unavailable to inserts until
+ * lvq_release, so a search that still runs on an earlier visibility snapshot
+ * (lvq_view_set_live) keeps reading the vector it sees there.
+ * ids: n int64.  out_n_deleted: 1 int64 (device), receives the number of
+ * live slots deleted. */
+lvq_status lvq_delete_hold(lvq_store *store, const int64_t *ids, int64_t n, int64_t *out_n_deleted,
+                           lvq_stream_t stream);
+
+/* Free slots held by lvq_delete_hold: every slot among ids that is not live
+ * and is reserved becomes free for inserts.  Pass only ids the caller held: a
+ * slot written by lvq_insert_deferred and not yet published is also reserved
+ * and not live, and would be freed too.  Ids out of range are ignored. */
+lvq_status lvq_release(lvq_store *store, const int64_t *ids, int64_t n, lvq_stream_t stream);
+
+/* Visibility snapshots.  The store's visibility is a bitmap of
+ * ceil(capacity / 32) uint32 words (bit s % 32 of word s / 32 set: slot s is
+ * live).  lvq_live_words returns that word count (host int64).
+ * lvq_snapshot_live copies the current bitmap to dst (device, that many
+ * words, caller-owned) in stream order.  lvq_view_set_live makes every
+ * search through `view` (a handle from lvq_store_view) use the bitmap at
+ * `live` (device, caller-owned, kept alive while searches use it) instead of
+ * the store's; NULL restores the store's.  Updates through any handle act on
+ * the store's own bitmap, never on a snapshot.  A search on a snapshot sees
+ * exactly the slots live when it was taken, provided none of them has been
+ * reused since (delete with lvq_delete_hold; release only after the last
+ * search on the snapshot).  Returns LVQ_EINVAL for a handle that is not a
+ * view. */
+lvq_status lvq_live_words(const lvq_store *store, int64_t *out_words);
+lvq_status lvq_snapshot_live(const lvq_store *store, uint32_t *dst, lvq_stream_t stream);
+lvq_status lvq_view_set_live(lvq_store *view, const uint32_t *live);
+
 /* M-LVQ centre update (Sec. 3.2, multi-means LVQ; re-encoding a centre's
  * vectors after an update is what makes M-LVQ suited to streaming data):
  * replace centre m by new_mean and re-encode every live slot tagged with m

@@ -317,14 +317,31 @@ __global__ void publish_reserved_kernel(uint32_t* live, uint32_t* reserved, int6
   }
 }
 
-__global__ void delete_kernel(uint32_t* live, int64_t capacity, const int64_t* ids, int64_t n,
+// Deletes clear the live bit; with `hold` (non-null: the reserved bitmap)
+// a slot that was live also becomes reserved, so no insert reuses it before
+// release_kernel frees it.
+__global__ void delete_kernel(uint32_t* live, uint32_t* hold, int64_t capacity, const int64_t* ids, int64_t n,
                               unsigned long long* count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = ids[i];
     if (s < 0 || s >= capacity) continue;
     const uint32_t bit = 1u << (s & 31);
     const uint32_t old = atomicAnd(live + (s >> 5), ~bit);
-    if (old & bit) atomicAdd(count, 1ull);
+    if (old & bit) {
+      if (hold) atomicOr(hold + (s >> 5), bit);
+      atomicAdd(count, 1ull);
+    }
+  }
+}
+
+// Held slots (reserved, not live) among ids become free.
+__global__ void release_kernel(const uint32_t* live, uint32_t* reserved, int64_t capacity, const int64_t* ids,
+                               int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = ids[i];
+    if (s < 0 || s >= capacity) continue;
+    const uint32_t bit = 1u << (s & 31);
+    if (!(live[s >> 5] & bit)) atomicAnd(reserved + (s >> 5), ~bit);
   }
 }
 
@@ -495,13 +512,20 @@ cudaError_t launch_publish_reserved(const DeviceStore& st, const int64_t* ids, i
 }
 
 cudaError_t launch_delete(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* out_n,
-                          unsigned long long* count, int64_t* n_live, cudaStream_t stream) {
+                          unsigned long long* count, int64_t* n_live, cudaStream_t stream, bool hold) {
   cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
   if (n > 0) {
     const int blocks = (int)(ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096);
-    delete_kernel<<<blocks, 256, 0, stream>>>(st.live, st.capacity, ids, n, count);
+    delete_kernel<<<blocks, 256, 0, stream>>>(st.live, hold ? st.reserved : nullptr, st.capacity, ids, n, count);
   }
   delete_finish_kernel<<<1, 1, 0, stream>>>(count, out_n, n_live);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_release(const DeviceStore& st, const int64_t* ids, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)(ceil_div(n, 256) < 4096 ? ceil_div(n, 256) : 4096);
+  release_kernel<<<blocks, 256, 0, stream>>>(st.live, st.reserved, st.capacity, ids, n);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ cudaError_t launch_publish(const DeviceStore& st, const int64_t* ids, int64_t n,
 cudaError_t launch_publish_reserved(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* n_live,
                                     cudaStream_t stream);
 cudaError_t launch_delete(const DeviceStore& st, const int64_t* ids, int64_t n, int64_t* out_n,
-                          unsigned long long* count, int64_t* n_live, cudaStream_t stream);
+                          unsigned long long* count, int64_t* n_live, cudaStream_t stream, bool hold);
+cudaError_t launch_release(const DeviceStore& st, const int64_t* ids, int64_t n, cudaStream_t stream);
 cudaError_t launch_export(const DeviceStore& st, const int64_t* ids, int64_t n, uint8_t* codes1,
                           uint8_t* codes2, float* lower, float* step, uint8_t* mean_id, cudaStream_t stream);
 

@@ -413,12 +413,12 @@ static lvq_status insert_impl(lvq_store* s, const float* x, int64_t n, int64_t* 
   int32_t* scratch = reinterpret_cast<int32_t*>(ctr + kCtrWords);
   {
     Prof p(s, st, LVQ_K_INSERT, 5);
-    LVQ_CUDA(s, launch_alloc_slots(s->ds, n, out_ids, scratch, abort_flag, st), "alloc_slots");
+    LVQ_CUDA(s, launch_alloc_slots(r->ds, n, out_ids, scratch, abort_flag, st), "alloc_slots");
     EncodeOut o;
     o.slots = out_ids;
     o.abort_flag = abort_flag;
-    LVQ_CUDA(s, launch_encode(s->ds, x, n, o, st), "encode(insert)");
-    LVQ_CUDA(s, launch_publish(s->ds, out_ids, n, abort_flag, ctr + kCtrLive, deferred, st), "publish");
+    LVQ_CUDA(s, launch_encode(r->ds, x, n, o, st), "encode(insert)");
+    LVQ_CUDA(s, launch_publish(r->ds, out_ids, n, abort_flag, ctr + kCtrLive, deferred, st), "publish");
   }
   // the n lowest free slots lie below (live + reserved + n) <= bound + n
   int64_t cur = r->rows_bound.load();
@@ -444,7 +444,7 @@ lvq_status lvq_publish(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t
   if (!ids) return fail(s, LVQ_EINVAL, "null pointer");
   if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
   Prof p(s, (cudaStream_t)stream, LVQ_K_INSERT);
-  LVQ_CUDA(s, launch_publish_reserved(s->ds, ids, n, root_of(s)->counters + kCtrLive, (cudaStream_t)stream),
+  LVQ_CUDA(s, launch_publish_reserved(root_of(s)->ds, ids, n, root_of(s)->counters + kCtrLive, (cudaStream_t)stream),
            "publish_reserved");
   return LVQ_OK;
 }
@@ -457,9 +457,62 @@ lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_
   int64_t* ctr = root_of(s)->counters;
   Prof p(s, (cudaStream_t)stream, LVQ_K_DELETE, n > 0 ? 2 : 1);
   LVQ_CUDA(s,
-           launch_delete(s->ds, ids, n, out_n_deleted, reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount),
-                         ctr + kCtrLive, (cudaStream_t)stream),
+           launch_delete(root_of(s)->ds, ids, n, out_n_deleted,
+                         reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount), ctr + kCtrLive,
+                         (cudaStream_t)stream, false),
            "delete");
+  return LVQ_OK;
+}
+
+lvq_status lvq_delete_hold(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_n_deleted,
+                           lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (!out_n_deleted || (n > 0 && !ids)) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  int64_t* ctr = root_of(s)->counters;
+  Prof p(s, (cudaStream_t)stream, LVQ_K_DELETE, n > 0 ? 2 : 1);
+  LVQ_CUDA(s,
+           launch_delete(root_of(s)->ds, ids, n, out_n_deleted,
+                         reinterpret_cast<unsigned long long*>(ctr + kCtrDelCount), ctr + kCtrLive,
+                         (cudaStream_t)stream, true),
+           "delete_hold");
+  return LVQ_OK;
+}
+
+lvq_status lvq_release(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
+  if (n > 0 && !ids) return fail(s, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
+  LVQ_CUDA(s, launch_release(root_of(s)->ds, ids, n, (cudaStream_t)stream), "release");
+  return LVQ_OK;
+}
+
+lvq_status lvq_live_words(const lvq_store* s, int64_t* out_words) {
+  if (!s || !out_words) return LVQ_EINVAL;
+  *out_words = (s->ds.capacity + 31) / 32;
+  return LVQ_OK;
+}
+
+lvq_status lvq_snapshot_live(const lvq_store* s, uint32_t* dst, lvq_stream_t stream) {
+  if (!s) return LVQ_EINVAL;
+  lvq_store* m = const_cast<lvq_store*>(s);
+  if (!dst) return fail(m, LVQ_EINVAL, "null pointer");
+  if (!valid_stream_device(s)) return fail(m, LVQ_EINVAL, "current device differs from the store's device");
+  const lvq_store* r = root_of(s);
+  LVQ_CUDA(m,
+           cudaMemcpyAsync(dst, r->ds.live, (size_t)((r->ds.capacity + 31) / 32) * 4, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream),
+           "snapshot_live");
+  return LVQ_OK;
+}
+
+lvq_status lvq_view_set_live(lvq_store* view, const uint32_t* live) {
+  if (!view) return LVQ_EINVAL;
+  if (!view->base) return fail(view, LVQ_EINVAL, "not a view");
+  std::lock_guard<std::mutex> g(view->mu);
+  view->ds.live = live ? const_cast<uint32_t*>(live) : root_of(view)->ds.live;
   return LVQ_OK;
 }
 
@@ -468,7 +521,7 @@ lvq_status lvq_update_mean(lvq_store* s, int32_t m, const float* new_mean, int64
   if (!new_mean || !out_count) return fail(s, LVQ_EINVAL, "null pointer");
   if (m < 0 || m >= s->ds.n_means) return fail(s, LVQ_EINVAL, "mean index out of range");
   if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
-  const DeviceStore& st = s->ds;
+  const DeviceStore& st = root_of(s)->ds;
   const cudaStream_t str = (cudaStream_t)stream;
   std::lock_guard<std::mutex> g(s->mu);
   const int64_t n_rows = root_of(s)->rows_bound.load();

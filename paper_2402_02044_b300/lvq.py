@@ -58,6 +58,11 @@ _SIGS = {
     "lvq_publish": [_P, _P, _I64, _P],
     "lvq_store_view": [_P, ctypes.POINTER(_P)],
     "lvq_delete": [_P, _P, _I64, _P, _P],
+    "lvq_delete_hold": [_P, _P, _I64, _P, _P],
+    "lvq_release": [_P, _P, _I64, _P],
+    "lvq_live_words": [_P, ctypes.POINTER(_I64)],
+    "lvq_snapshot_live": [_P, _P, _P],
+    "lvq_view_set_live": [_P, _P],
     "lvq_search_exhaustive": [_P, _P, _I64, _I32, _I32, _I32, _P, _P, _P],
     "lvq_search_first_level": [_P, _P, _I64, _I32, _I32, _P, _P, _P],
     "lvq_update_mean": [_P, _I32, _P, ctypes.POINTER(_I64), _P],
@@ -174,6 +179,30 @@ def lvq_store_view(store) -> int:
 def lvq_delete(store, ids, out_n_deleted, stream=None):
     _check(load().lvq_delete(store, _ptr(ids, torch.int64, "ids"), ids.numel(),
                              _ptr(out_n_deleted, torch.int64, "out_n_deleted"), _stream(stream)), "lvq_delete")
+
+
+def lvq_delete_hold(store, ids, out_n_deleted, stream=None):
+    _check(load().lvq_delete_hold(store, _ptr(ids, torch.int64, "ids"), ids.numel(),
+                                  _ptr(out_n_deleted, torch.int64, "out_n_deleted"), _stream(stream)),
+           "lvq_delete_hold")
+
+
+def lvq_release(store, ids, stream=None):
+    _check(load().lvq_release(store, _ptr(ids, torch.int64, "ids"), ids.numel(), _stream(stream)), "lvq_release")
+
+
+def lvq_live_words(store) -> int:
+    out = _I64()
+    _check(load().lvq_live_words(store, ctypes.byref(out)), "lvq_live_words")
+    return out.value
+
+
+def lvq_snapshot_live(store, dst, stream=None):
+    _check(load().lvq_snapshot_live(store, _ptr(dst, torch.int32, "dst"), _stream(stream)), "lvq_snapshot_live")
+
+
+def lvq_view_set_live(view, live):
+    _check(load().lvq_view_set_live(view, _ptr(live, torch.int32, "live", allow_none=True)), "lvq_view_set_live")
 
 
 def lvq_search_exhaustive(store, q, k1, k, precision, out_ids, out_scores, stream=None):
@@ -335,6 +364,27 @@ class Store:
         out = torch.empty(1, dtype=torch.int64, device=ids.device)
         lvq_delete(self.handle, ids, out, stream)
         return out
+
+    def delete_hold(self, ids: torch.Tensor, stream=None) -> torch.Tensor:
+        """Delete, keeping the slots from reuse until release()."""
+        out = torch.empty(1, dtype=torch.int64, device=ids.device)
+        lvq_delete_hold(self.handle, ids, out, stream)
+        return out
+
+    def release(self, ids: torch.Tensor, stream=None):
+        lvq_release(self.handle, ids, stream)
+
+    def live_snapshot(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """A device copy of the visibility bitmap (int32 words), in stream order."""
+        if out is None:
+            out = torch.empty(lvq_live_words(self.handle), dtype=torch.int32, device="cuda")
+        lvq_snapshot_live(self.handle, out, stream)
+        return out
+
+    def set_live(self, live: Optional[torch.Tensor]):
+        """(views) search on the given visibility bitmap; None: the store's."""
+        lvq_view_set_live(self.handle, live)
+        self._live_ref = live
 
     def search(self, q: torch.Tensor, k: int, k1: int = 0, precision="fp32", stream=None):
         ids = torch.empty((q.shape[0], k), dtype=torch.int64, device=q.device)

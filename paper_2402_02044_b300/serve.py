@@ -11,20 +11,28 @@ Model
   memory) with its own CUDA stream, so batches overlap on the device.  A
   request's rows are re-split from the batch's results (the top-k of a query
   is the first k of its top-k_max list).  A request of more than max_batch
-  rows is cut into parts of at most max_batch rows that queue one after
-  another; its future completes when the last part does.  Beyond one or two
-  query tiles a batch gains no throughput (the scan's cost grows with its
-  rows), so a small max_batch bounds how long a request waits behind others.
+  rows is cut into parts of at most max_batch rows; once its first part has
+  run, lanes alternate between its remaining parts and new requests, so a
+  large request does not hold up small ones behind it.  Its future completes
+  when the last part does.
 * Insert requests are encoded at once on an update stream with
   ``lvq_insert_deferred``: their slots are written while searches run, but
   stay invisible.  Deletes are queued.
-* Visibility changes at *epoch* boundaries: when updates are pending, the
-  scheduler stops starting new query batches, waits for the ones in flight,
-  publishes the pending inserts and applies the deletes, then resumes; the
-  remaining parts of a request already started are launched first, so all
-  parts of a request run in one epoch.  Every query therefore sees exactly
+* Visibility changes at *epoch* boundaries, without stopping the queries:
+  each epoch has a device copy of the visibility bitmap (two, used in turn),
+  and a batch searches through its lane's view on its epoch's copy.  At a
+  boundary the update stream publishes the pending inserts, deletes with
+  ``lvq_delete_hold`` (the slots stay reserved, so no insert overwrites a
+  vector an older snapshot still shows), copies the bitmap for the new
+  epoch, and frees the slots held at the previous boundary; before it
+  rewrites a bitmap or frees slots it waits, on the device, for the batches
+  of the epoch before the current one.  New batches wait on the boundary's
+  event.  All parts of a request run on the bitmap of the epoch its first
+  part ran in (kept for one more epoch; a second boundary waits until such
+  a request has launched its last part).  Every query therefore sees exactly
   the store state of the epoch it ran in, and a request's result is the same
-  whether it ran alone, split or batched with others.
+  whether it ran alone, split or batched with others.  A deleted slot becomes
+  free for inserts one boundary later.
 * Admission: each request holds device bytes (its inputs and outputs) while
   in flight; a request waits while the total would exceed the HBM budget,
   and one that could never fit is rejected.
@@ -67,7 +75,7 @@ class _Group:
     def __init__(self, parts: int, future: Future, rows: int):
         self.results = [None] * parts
         self.remaining = parts
-        self.launched = 0
+        self.rest = collections.deque()  # parts not yet queued: they follow the first
         self.future = future
         self.rows = rows
         self.epoch = -1
@@ -167,12 +175,13 @@ class _Lane:
         self.sc_pin = torch.empty((max_batch, kmax), dtype=torch.float32).pin_memory()
         self.graphs = {}
         self.busy = None  # (event, batch, rows, kb)
+        self.busy_epoch = -1
 
 
 class Server:
     def __init__(self, store: Store, lanes: int = 2, max_batch: int = 4096, k1: int = 100, kmax: int = 100,
                  precision: str = "auto", hbm_budget: Optional[int] = None, use_graphs: bool = False,
-                 tuning: Optional[dict] = None, warmup: bool = True):
+                 tuning: Optional[dict] = None, warmup: bool = True, update_rows: int = 16384):
         self.store = store
         self.d = store.d
         self.k1 = k1 if store.bits2 else 0
@@ -186,9 +195,18 @@ class Server:
             hbm_budget = free // 2
         self.admission = Admission(hbm_budget)
         self.lanes = [_Lane(store, self.d, max_batch, kmax, max(self.k1, kmax)) for _ in range(lanes)]
+        self.upd_stream = torch.cuda.Stream()
+        self.upd_pin = torch.empty((max(1, update_rows), self.d), dtype=torch.float32).pin_memory()
+        self.upd_pin_ev = None
+        # the visibility bitmaps of the current and the previous epoch
+        self.snaps = [store.live_snapshot(stream=self.upd_stream)]
+        self.snaps.append(torch.empty_like(self.snaps[0]))
+        self.upd_stream.synchronize()
+        for lane in self.lanes:
+            lane.view.set_live(self.snaps[0])
+        self.held = collections.deque()  # (epoch entered, ids) of deletes whose slots are held
         if warmup:
             self._warmup()
-        self.upd_stream = torch.cuda.Stream()
         self.pending_q = collections.deque()
         self.pending_upd = collections.deque()
         self.staged = []          # (ids_dev, request) of deferred inserts awaiting publication
@@ -196,7 +214,9 @@ class Server:
         self.inflight_upd = []    # (event, request, result tensor, kind)
         self.epoch = 0
         self.epoch_event = None
-        self.open_groups = set()  # split requests with some but not all parts launched
+        self.open_groups = collections.deque()  # split requests with parts still to launch
+        self.epoch_events = {}  # epoch -> event of the boundary that opened it (last two)
+        self._parts_turn = False
         self.stats = LatencyStats()
         self.rejected = 0
         self._lock = threading.Lock()
@@ -237,7 +257,8 @@ class Server:
                 self.rejected += 1
                 fut.set_exception(MemoryError("request larger than the HBM budget"))
                 return fut
-            self.pending_q.extend(parts)
+            grp.rest.extend(parts[1:])
+            self.pending_q.append(parts[0])
             self._wake.notify_all()
         return fut
 
@@ -260,8 +281,8 @@ class Server:
         t_end = time.time() + timeout
         while time.time() < t_end:
             with self._lock:
-                idle = (not self.pending_q and not self.pending_upd and not self.staged and not self.deletes
-                        and not self.inflight_upd and all(l.busy is None for l in self.lanes))
+                idle = (not self.pending_q and not self.open_groups and not self.pending_upd and not self.staged
+                        and not self.deletes and not self.inflight_upd and all(l.busy is None for l in self.lanes))
             if idle:
                 return
             time.sleep(0.001)
@@ -272,7 +293,13 @@ class Server:
             self._stop = True
             self._wake.notify_all()
         self._thread.join()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.upd_stream):
+            while self.held:
+                self.store.release(self.held.popleft()[1], stream=self.upd_stream)
+        self.upd_stream.synchronize()
         for l in self.lanes:
+            l.view.set_live(None)
             l.view.close()
 
     def _submit(self, r: Request) -> Future:
@@ -293,8 +320,8 @@ class Server:
             with self._lock:
                 if self._stop:
                     return
-                if not (self.pending_q or self.pending_upd or self.staged or self.deletes or self.inflight_upd
-                        or any(l.busy is not None for l in self.lanes)):
+                if not (self.pending_q or self.open_groups or self.pending_upd or self.staged or self.deletes
+                        or self.inflight_upd or any(l.busy is not None for l in self.lanes)):
                     self._wake.wait(timeout=0.01)
                     continue
             progressed = self._step()
@@ -308,15 +335,12 @@ class Server:
         progressed = self._complete()
         progressed |= self._stage_updates()
         updates_waiting = bool(self.staged or self.deletes)
-        if (updates_waiting and not self.open_groups and all(l.busy is None for l in self.lanes)
-                and not self.inflight_upd):
+        # a split request runs on its first part's bitmap, which the next
+        # boundary keeps and the one after rewrites
+        if updates_waiting and all(g.epoch == self.epoch for g in self.open_groups):
             self._epoch_boundary()
             progressed = True
-        elif not updates_waiting:
-            progressed |= self._launch_queries()
-        elif self.open_groups:
-            # the rest of a split request runs in the epoch its first part ran in
-            progressed |= self._launch_queries(only_open=True)
+        progressed |= self._launch_queries()
         return progressed
 
     def _complete(self) -> bool:
@@ -356,8 +380,7 @@ class Server:
                 continue
             with self._lock:
                 self.admission.give(r.nbytes)
-            if kind == DELETE:
-                r.future.set_result(int(res.item()))
+            r.future.set_result(int(res.item()) if kind == DELETE else res.numpy())
             done_any = True
         self.inflight_upd = keep
         return done_any
@@ -374,7 +397,18 @@ class Server:
         with torch.cuda.stream(self.upd_stream):
             for r in reqs:
                 if r.kind == INSERT:
-                    x = torch.from_numpy(r.data).pin_memory().cuda(non_blocking=True)
+                    x = torch.empty(r.data.shape, dtype=torch.float32, device="cuda")
+                    # through a pinned staging buffer allocated once (pinning
+                    # each request's rows would allocate page-locked memory on
+                    # the scheduler's path)
+                    for a in range(0, len(r.data), len(self.upd_pin)):
+                        b = min(len(r.data), a + len(self.upd_pin))
+                        if self.upd_pin_ev is not None:
+                            self.upd_pin_ev.synchronize()
+                        self.upd_pin[:b - a].copy_(torch.from_numpy(r.data[a:b]))
+                        x[a:b].copy_(self.upd_pin[:b - a], non_blocking=True)
+                        self.upd_pin_ev = torch.cuda.Event()
+                        self.upd_pin_ev.record(self.upd_stream)
                     ids = self.store.insert_deferred(x, stream=self.upd_stream)
                     self.staged.append((ids, x, r))
                 else:
@@ -382,70 +416,107 @@ class Server:
         return True
 
     def _epoch_boundary(self):
-        """Publish staged inserts and apply queued deletes (no query in flight)."""
+        """Publish staged inserts, apply queued deletes and take the new
+        epoch's bitmap, on the update stream, while batches run."""
         s = self.upd_stream
+        e = self.epoch
+        nxt = self.snaps[(e + 1) & 1]
         with torch.cuda.stream(s):
+            # nxt and the slots held at the previous boundary may still be in
+            # use by batches of epoch e - 1
+            for lane in self.lanes:
+                if lane.busy is not None and lane.busy_epoch < e:
+                    s.wait_event(lane.busy[0])
+            while self.held:
+                self.store.release(self.held.popleft()[1], stream=s)
             for ids, x, r in self.staged:
                 self.store.publish(ids, stream=s)
-                ids_host = ids.to("cpu", non_blocking=False)
-                r.future.set_result(ids_host.numpy())
-                with self._lock:
-                    self.admission.give(r.nbytes)
+                ids_host = torch.empty(ids.shape, dtype=ids.dtype, pin_memory=True)
+                ids_host.copy_(ids, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
+                self.inflight_upd.append((ev, r, ids_host, INSERT))
             for r in self.deletes:
                 ids = torch.from_numpy(r.data).cuda(non_blocking=True)
-                out = self.store.delete(ids, stream=s)
+                out = self.store.delete_hold(ids, stream=s)
+                self.held.append((e + 1, ids))
                 ev = torch.cuda.Event()
                 ev.record(s)
                 self.inflight_upd.append((ev, r, out, DELETE))
+            self.store.live_snapshot(nxt, stream=s)
             ev = torch.cuda.Event()
             ev.record(s)
         self.staged, self.deletes = [], []
         self.epoch_event = ev
-        self.epoch += 1
+        self.epoch = e + 1
+        self.epoch_events[e + 1] = ev
+        self.epoch_events.pop(e - 1, None)
 
-    def _launch_queries(self, only_open: bool = False) -> bool:
+    def _launch_queries(self) -> bool:
+        """Start a batch on every idle lane: either the next part of the oldest
+        open split request (on that request's epoch) or new requests from the
+        queue head (on the current epoch), taking turns when both wait."""
         launched = False
-        accept = (lambda r: r.group is not None and r.group in self.open_groups) if only_open else None
         for lane in self.lanes:
             if lane.busy is not None:
                 continue
+            batch, epoch = [], self.epoch
             with self._lock:
-                batch = form_batch(self.pending_q, self.max_batch, self.admission, accept)
+                take_part = bool(self.open_groups) and (self._parts_turn or not self.pending_q)
+                if take_part:
+                    g = self.open_groups[0]
+                    if self.admission.try_take(g.rest[0].nbytes):
+                        batch, epoch = [g.rest.popleft()], g.epoch
+                        if not g.rest:
+                            self.open_groups.popleft()
+                if not batch:
+                    batch = form_batch(self.pending_q, self.max_batch, self.admission)
+                    for r in batch:
+                        g = r.group
+                        if g is not None and g.rest:
+                            g.epoch = epoch
+                            self.open_groups.append(g)
+                if not batch and not take_part and self.open_groups:
+                    g = self.open_groups[0]
+                    if self.admission.try_take(g.rest[0].nbytes):
+                        batch, epoch = [g.rest.popleft()], g.epoch
+                        if not g.rest:
+                            self.open_groups.popleft()
+                self._parts_turn = not self._parts_turn
             if not batch:
                 break
             rows = sum(r.data.shape[0] for r in batch)
             kb = max(r.k for r in batch)
             for r in batch:
-                r.epoch = self.epoch
-                g = r.group
-                if g is not None:
-                    g.epoch = self.epoch
-                    g.launched += 1
-                    if g.launched < len(g.results):
-                        self.open_groups.add(g)
-                    else:
-                        self.open_groups.discard(g)
-            self._run_batch(lane, batch, rows, kb)
+                r.epoch = epoch
+                if r.group is not None:
+                    r.group.epoch = epoch
+            self._run_batch(lane, batch, rows, kb, epoch)
             launched = True
         return launched
 
-    def _run_batch(self, lane: _Lane, batch, rows: int, kb: int):
+    def _run_batch(self, lane: _Lane, batch, rows: int, kb: int, epoch: int):
         off = 0
         for r in batch:
             n = r.data.shape[0]
             lane.q_pin[off:off + n].copy_(torch.from_numpy(r.data))
             off += n
         s = lane.stream
+        par = epoch & 1
+        lane.view.set_live(self.snaps[par])
+        lane.busy_epoch = epoch
         with torch.cuda.stream(s):
-            if self.epoch_event is not None:
-                s.wait_event(self.epoch_event)
+            ev0 = self.epoch_events.get(epoch)
+            if ev0 is not None:
+                s.wait_event(ev0)
             lane.q_dev[:rows].copy_(lane.q_pin[:rows], non_blocking=True)
             kk = self.kmax if self.use_graphs else kb
             nb = bucket(rows) if self.use_graphs else rows
             if self.use_graphs:
-                g = lane.graphs.get(nb)
+                # a graph holds the bitmap it was captured with: one per bitmap
+                g = lane.graphs.get((nb, par))
                 if g is None:
-                    g = self._capture(lane, nb)
+                    g = self._capture(lane, nb, par)
                 g.replay()
             else:
                 self._search(lane, nb, kk)
@@ -471,12 +542,12 @@ class Server:
             lane.ids_dev[:nb, :kk].copy_(ids)
             lane.sc_dev[:nb, :kk].copy_(sc)
 
-    def _capture(self, lane: _Lane, nb: int):
+    def _capture(self, lane: _Lane, nb: int, par: int):
         # a warm-up call outside the capture sets kernel attributes and scratch
         self._search(lane, nb, self.kmax)
         lane.stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=lane.stream):
             self._search(lane, nb, self.kmax)
-        lane.graphs[nb] = g
+        lane.graphs[(nb, par)] = g
         return g

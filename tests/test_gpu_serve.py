@@ -90,30 +90,39 @@ def test_updates_become_visible_at_epoch_boundaries():
     from paper_2402_02044_b300.serve import Server
     mix, x, means, st = _setup(n=20000, d=64, metric="l2")
     srv = Server(st, lanes=2, max_batch=512, k1=50, kmax=10, precision="fp16")
+    # the replay's live marks occupied slots: live ones and deleted ones
+    # still held for older snapshots
     rep = O.SlotReplay(st.capacity)
     rep.insert(20000)
     rows = {i: x[i] for i in range(20000)}
     g = np.random.default_rng(5)
+    held = np.zeros(0, np.int64)  # deleted at the previous boundary
     for step in range(3):
-        dele = g.choice(np.nonzero(rep.live)[0], 500, replace=False)
+        live_now = rep.live.copy()
+        live_now[held] = False
+        dele = g.choice(np.nonzero(live_now)[0], 500, replace=False)
         new = mix.rows(100 * step, 100 * step + 700, stream=12)
         fd = srv.submit_delete(dele)
         fi = srv.submit_insert(new)
         fq = srv.submit_query(new[:5], 10)          # queued behind the updates or before them
         ids_new = fi.result(timeout=60)
         assert fd.result(timeout=60) == 500
-        # deletes and inserts of one epoch are applied together: deletes free
-        # slots only after the epoch's inserts took theirs
+        # an epoch's inserts take the lowest slots neither live nor held; its
+        # deletes are held until the next boundary, which frees the slots held
+        # at this one
         ref_new = rep.insert(700)
-        rep.delete(dele)
+        rep.delete(held)
+        held = dele
         assert np.array_equal(np.sort(ids_new), np.sort(ref_new))
         for r, v in zip(ids_new, new):
             rows[int(r)] = v
         fq.result(timeout=60)
     srv.drain()
-    assert st.stats() == rep.live.sum()
+    live = rep.live.copy()
+    live[held] = False
+    assert st.stats() == live.sum()
     # the state after the last epoch: a fresh query equals the oracle
-    live_ids = np.nonzero(rep.live)[0]
+    live_ids = np.nonzero(live)[0]
     q = mix.queries(4)
     got_i, got_s, _ = srv.submit_query(q, 10).result(timeout=60)
     xs = np.zeros((st.capacity, 64), np.float32)
@@ -121,8 +130,40 @@ def test_updates_become_visible_at_epoch_boundaries():
         xs[i] = rows[int(i)]
     enc = O.encode(xs, means, 4, 8)
     from helpers import TOL_FP16, check_two_level
-    check_two_level(q, got_i, enc, means, "l2", 50, 10, TOL_FP16, live=rep.live)
+    check_two_level(q, got_i, enc, means, "l2", 50, 10, TOL_FP16, live=live)
     srv.close()
+    st.close()
+
+
+def test_snapshot_views_and_held_deletes():
+    """A view on a visibility snapshot keeps seeing the slots live when it was
+    taken; lvq_delete_hold keeps deleted slots from reuse until lvq_release."""
+    mix, x, means, st = _setup(n=3000, d=64)
+    q = torch.from_numpy(mix.queries(4)).cuda()
+    snap = st.live_snapshot()
+    torch.cuda.synchronize()
+    v = st.view()
+    v.set_live(snap)
+    bi, bs = v.search(q, 10, 50, "fp16")
+    top = np.unique(bi[:, 0].cpu().numpy())
+    assert int(st.delete_hold(torch.from_numpy(top).cuda()).item()) == len(top)
+    vi, vs = v.search(q, 10, 50, "fp16")
+    assert torch.equal(vi, bi) and torch.equal(vs, bs)
+    si, _ = st.search(q, 10, 50, "fp16")
+    assert not np.isin(si.cpu().numpy(), top).any()
+    # held slots are skipped by inserts (the lowest free slots lie above 3000)
+    add = torch.from_numpy(mix.rows(9000, 9000 + len(top), stream=31)).cuda()
+    ids1 = st.insert(add).cpu().numpy()
+    assert not np.isin(ids1, top).any()
+    st.delete(torch.from_numpy(ids1).cuda())
+    st.release(torch.from_numpy(top).cuda())
+    ids2 = st.insert(add).cpu().numpy()
+    assert np.array_equal(np.sort(ids2), np.sort(top))
+    v.set_live(None)
+    vi, vs = v.search(q, 10, 50, "fp16")
+    si, ss = st.search(q, 10, 50, "fp16")
+    assert torch.equal(vi, si) and torch.equal(vs, ss)
+    v.close()
     st.close()
 
 
