@@ -204,28 +204,48 @@ __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const f
   __shared__ int cnt;
   __shared__ uint64_t thr;
   __shared__ int hist[288];
-  __shared__ int len[kMaxMergeLists];  // valid keys per list (counts given)
+  __shared__ int start[kMaxMergeLists + 1];  // first position of each list's keys (counts given)
+  __shared__ int scan_sh[T / 32 + 1];
   if (threadIdx.x == 0) {
     cnt = 0;
     thr = kNoKey;
   }
   for (int j = threadIdx.x; j < st.d; j += blockDim.x) qsh[j] = q[(int64_t)qi * st.d + j];
-  if (counts)
-    for (int i = threadIdx.x; i < splits; i += blockDim.x) len[i] = counts[(int64_t)qi * splits + i];
-  __syncthreads();
   const uint64_t* src = partial + (int64_t)qi * splits * k1;
-  const int total = splits * k1;
+  // With counts only the valid keys are visited: position p of the packed
+  // sequence is key p - start[l] of list l (start: exclusive prefix sums).
+  int total = splits * k1;
+  if (counts) {
+    int run = 0;
+    for (int c0 = 0; c0 < splits; c0 += T) {
+      const int i = c0 + threadIdx.x;
+      const int v = i < splits ? counts[(int64_t)qi * splits + i] : 0;
+      int sum;
+      const int at = run + block_exclusive_scan(v, scan_sh, sum);
+      if (i < splits) start[i] = at;
+      run += sum;
+    }
+    if (threadIdx.x == 0) start[splits] = run;
+    total = run;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  // rounds of kMergeRound keys, kMergePer independent loads per thread; with
-  // counts, positions past a list's length are not read
+  // rounds of kMergeRound keys, kMergePer independent loads per thread
   for (int base = 0; base < total; base += kMergeRound) {
     uint64_t v[kMergePer];
 #pragma unroll
     for (int r = 0; r < kMergePer; ++r) {
       const int i = base + r * T + threadIdx.x;
-      bool in = i < total;
-      if (in && counts) in = (i % k1) < len[i / k1];
-      v[r] = in ? __ldg(src + i) : kNoKey;
+      int at = i;
+      if (counts && i < total) {
+        int lo = 0, hi = splits;  // the last list with start <= i
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (start[mid] <= i) lo = mid; else hi = mid;
+        }
+        at = lo * k1 + (i - start[lo]);
+      }
+      v[r] = i < total ? __ldg(src + at) : kNoKey;
     }
     const uint64_t t = thr;
 #pragma unroll

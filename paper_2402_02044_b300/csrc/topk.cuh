@@ -623,14 +623,23 @@ __device__ __forceinline__ int block_select_dedupe(uint64_t* buf, int cap, int n
 // k + 1 ints of shared memory.
 __device__ __forceinline__ void write_results(const uint64_t* keys, int n, int k, int metric, int64_t* out_ids,
                                               float* out_scores, int* sh_pos) {
-  if (threadIdx.x == 0) {
+  // one warp finds the positions of the first k distinct keys (repeats are
+  // adjacent in sorted order), 32 keys per step
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     int w = 0;
-    for (int i = 0; i < n && w < k; ++i) {
-      if (keys[i] == kNoKey) break;
-      if (i && keys[i] == keys[i - 1]) continue;
-      sh_pos[w++] = i;
+    bool done = false;
+    for (int base = 0; base < n && !done && w < k; base += 32) {
+      const int i = base + lane;
+      const uint64_t key = i < n ? keys[i] : kNoKey;
+      const bool keep = i < n && key != kNoKey && (i == 0 || key != keys[i - 1]);
+      const unsigned bal = __ballot_sync(kFull, keep);
+      const int pos = w + __popc(bal & ((1u << lane) - 1u));
+      if (keep && pos < k) sh_pos[pos] = i;
+      w += __popc(bal);
+      done = __any_sync(kFull, i < n && key == kNoKey);
     }
-    sh_pos[k] = w;
+    if (lane == 0) sh_pos[k] = w < k ? w : k;
   }
   __syncthreads();
   const int w = sh_pos[k];
