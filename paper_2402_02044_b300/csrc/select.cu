@@ -188,6 +188,18 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
 // that a lone query's re-rank has more warps); rounds of kMergeRound keys.
 constexpr int kMergeRound = 1024;
 
+// Cut buf[0..n) to its k best keys (called by all threads; the result is
+// meaningful in thread 0).  A 512-thread block (few queries: the block has an
+// SM to itself) sorts with every warp; a 128-thread block leaves the select
+// to one warp (6-bit radix select) while its other blocks keep the SM busy.
+template <int T>
+__device__ __forceinline__ int cut_keys(uint64_t* buf, int cap, int n, int k, int* hist, int* scan_sh, uint64_t* thr) {
+  if (T >= 512) return block_select_dedupe(buf, cap, n, k, scan_sh, thr);
+  int kept = 0;
+  if (threadIdx.x < 32) kept = warp_select6(buf, n, k, hist, thr);
+  return kept;
+}
+
 template <int T>
 __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const float* __restrict__ q,
                                                          const uint64_t* __restrict__ partial,
@@ -261,20 +273,18 @@ __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const f
     }
     __syncthreads();
     if (cnt > cap - kMergeRound) {
-      if (threadIdx.x < 32) {
-        uint64_t tk;
-        const int kept = warp_select6(buf, cnt, k1, hist, &tk);
-        if (threadIdx.x == 0) {
-          cnt = kept;
-          thr = tk;
-        }
+      uint64_t tk;
+      const int kept = cut_keys<T>(buf, cap, cnt, k1, hist, scan_sh, &tk);
+      if (threadIdx.x == 0) {
+        cnt = kept;
+        thr = tk;
       }
       __syncthreads();
     }
   }
-  if (threadIdx.x < 32) {
+  {
     uint64_t tk;
-    const int kept = warp_select6(buf, cnt, k1, hist, &tk);
+    const int kept = cut_keys<T>(buf, cap, cnt, k1, hist, scan_sh, &tk);
     if (threadIdx.x == 0) cnt = kept;
   }
   __syncthreads();
