@@ -199,6 +199,15 @@ def serve_leg(st, mix, n, avoid, duration_s=6.0, rate=40.0, update_every_s=0.25,
     # requests are in flight
     upd_rows = [mix.rows(u * B_upd, (u + 1) * B_upd, stream=13) for u in range(n_upd)]
     srv = Server(st, lanes=2, max_batch=1024, k1=100, kmax=100, precision="auto")
+    # steady state before the trace: one request of each size class and one
+    # update epoch (an insert and the delete of what it inserted), untimed
+    warm = [srv.submit_query(pool[:nq_w], 100) for nq_w in (1, 64, 1500)]
+    ids_w = srv.submit_insert(upd_rows[0][:16]).result(timeout=120)
+    srv.submit_delete(ids_w).result(timeout=120)
+    for f in warm:
+        f.result(timeout=120)
+    srv.drain()
+    srv.reset_stats()
     futs, upd = [], []
     t0 = time.perf_counter()
     next_upd, u = 0.0, 0

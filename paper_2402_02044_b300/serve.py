@@ -213,6 +213,7 @@ class Server:
         self.deletes = []         # delete requests awaiting the epoch boundary
         self.inflight_upd = []    # (event, request, result tensor, kind)
         self.epoch = 0
+        self.epoch_base = 0
         self.epoch_event = None
         self.open_groups = collections.deque()  # split requests with parts still to launch
         self.epoch_events = {}  # epoch -> event of the boundary that opened it (last two)
@@ -270,10 +271,16 @@ class Server:
         ids = np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
         return self._submit(Request(DELETE, ids, nbytes=request_bytes(DELETE, len(ids), self.d, 0)))
 
+    def reset_stats(self):
+        """Forget the latencies recorded so far (e.g. after a warm-up)."""
+        with self._lock:
+            self.stats = LatencyStats()
+            self.epoch_base = self.epoch
+
     def stats_summary(self) -> dict:
         with self._lock:
             s = self.stats.summary()
-            s.update(rejected=self.rejected, epochs=self.epoch, hbm_budget=self.admission.budget)
+            s.update(rejected=self.rejected, epochs=self.epoch - self.epoch_base, hbm_budget=self.admission.budget)
             return s
 
     def drain(self, timeout: float = 60.0):
