@@ -454,7 +454,7 @@ int small_stages(const DeviceStore& st, int qb, int k1) {
 bool small_supported(const DeviceStore& st, int64_t nq, int k1) {
   if (nq < 1 || nq > kSmallMaxQ || k1 < 1 || k1 > 1024) return false;
   if (st.bits1 != 4 && st.bits1 != 8) return false;
-  if (!mma_supported(st)) return false;  // needs the driver's tensor-map encoder too
+  if (!mma_supported(st)) return false;  // needs the CUDA driver's tensor-map encoder too
   return small_stages(st, small_qb(nq), k1) > 0;
 }
 
