@@ -333,14 +333,17 @@ __global__ void __launch_bounds__(kRerankThreads, 8) rerank_kernel(DeviceStore s
 // too, so the next query's first rows load while the block selects the
 // query's best keys.  A row is scored by L lanes (16-byte chunks l, l + L, ...); the
 // slot stride makes the lanes of a quarter warp hit distinct banks.
-// Products: <q, c> is computed exactly in integers: the query is rounded once
-// to 24-bit fixed point (Q_j = rint(q_j / s), s = max|q| / (2^23 - 1)), Q is
-// split into three byte planes (two unsigned, the top one signed) laid out in
-// code-word order, and dp4a accumulates each plane's products with the code
-// bytes in 32 bits; the planes are recombined in 64 bits, centred by the code
-// offset and scaled by s once per candidate.  Rounding q moves a score by at
-// most (s / 2) sqrt(d) ||x^|| <= 6e-8 sqrt(d) ||q|| ||x^||, a small fraction of
-// the float32 tolerance.
+// Products: <q, c> is computed exactly in integers: the query is scaled by a
+// power of two, s = 2^(e - 30) with 2^e <= max|q| < 2^(e+1), and rounded once
+// (Q_j = rint(q_j / s), |Q_j| < 2^31; elements within 2^7 of the largest are
+// exact), Q is split into four byte planes (three unsigned, the top one
+// signed) laid out in code-word order, and dp4a accumulates each plane's
+// products with the code bytes in 32 bits; the planes are recombined in 64
+// bits, centred by the code offset and scaled by s once per candidate.
+// Rounding q moves a score by at most (s / 2) D sum_j |c_j - off|
+// <= 2^-31 max|q| d D 2^(B1-1), under 4 % of the float32 tolerance even when
+// every rounding error lines up with the codes (one dominant query element,
+// one code far from the rest).
 constexpr int kGatherThreads = 128;
 constexpr int kGW = kGatherThreads / 32;
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;  // an empty row of a batch
@@ -377,17 +380,19 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 struct GatherAcc {
-  uint32_t a0, a1;
-  int a2;
+  uint32_t a0, a1, a2;
+  int a3;
 };
-// one code group (two 32-bit words of code bytes) against the three planes
-__device__ __forceinline__ void plane_step(GatherAcc& A, uint32_t x0, uint32_t x1, uint2 p0, uint2 p1, uint2 p2) {
+// one code group (two 32-bit words of code bytes) against the four planes
+__device__ __forceinline__ void plane_step(GatherAcc& A, uint32_t x0, uint32_t x1, uint2 p0, uint2 p1, uint2 p2,
+                                           uint2 p3) {
   A.a0 = g_dp4a_uu(x0, p0.x, g_dp4a_uu(x1, p0.y, A.a0));
   A.a1 = g_dp4a_uu(x0, p1.x, g_dp4a_uu(x1, p1.y, A.a1));
-  A.a2 = g_dp4a_us(x0, p2.x, g_dp4a_us(x1, p2.y, A.a2));
+  A.a2 = g_dp4a_uu(x0, p2.x, g_dp4a_uu(x1, p2.y, A.a2));
+  A.a3 = g_dp4a_us(x0, p3.x, g_dp4a_us(x1, p3.y, A.a3));
 }
-__device__ __forceinline__ void group4(GatherAcc& A, uint32_t w, uint2 p0, uint2 p1, uint2 p2) {
-  plane_step(A, w & 0x0F0F0F0Fu, (w >> 4) & 0x0F0F0F0Fu, p0, p1, p2);
+__device__ __forceinline__ void group4(GatherAcc& A, uint32_t w, uint2 p0, uint2 p1, uint2 p2, uint2 p3) {
+  plane_step(A, w & 0x0F0F0F0Fu, (w >> 4) & 0x0F0F0F0Fu, p0, p1, p2, p3);
 }
 
 __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore st, const float* __restrict__ q,
@@ -402,8 +407,8 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   const int R = gg.R, L = 32 / gg.R, P = gg.P;
   unsigned char* slots = smem;  // [kGW][P][slot_bytes]
   uint32_t* slot_ids = reinterpret_cast<uint32_t*>(slots + (size_t)kGW * P * gg.slot_bytes);  // [kGW][P][32]
-  uint2* planes = reinterpret_cast<uint2*>(slot_ids + kGW * P * 32);                       // [3][gpad]
-  uint64_t* buf = reinterpret_cast<uint64_t*>(planes + 3 * gpad);                         // [cap]
+  uint2* planes = reinterpret_cast<uint2*>(slot_ids + kGW * P * 32);                       // [4][gpad]
+  uint64_t* buf = reinterpret_cast<uint64_t*>(planes + 4 * gpad);                         // [cap]
   int* sh_pos = reinterpret_cast<int*>(buf + cap);                                          // [k + 2]
   __shared__ int cnt;
   __shared__ uint64_t thr;
@@ -505,27 +510,29 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
     mx = 0.0f;
 #pragma unroll
     for (int i = 0; i < kGW; ++i) mx = fmaxf(mx, qmax_sh[i]);
-    const float qscale = mx > 0.0f ? mx / 8388607.0f : 0.0f;
-    const float qinv = mx > 0.0f ? 8388607.0f / mx : 0.0f;
+    // s = 2^qe: q_j / s is exact in float32, so only its fraction is rounded
+    const int qe = mx > 0.0f ? ilogbf(mx) - 30 : 0;
+    const float qscale = mx > 0.0f ? ldexpf(1.0f, qe) : 0.0f;
     {
       long long part = 0;
       for (int g = threadIdx.x; g < gpad; g += blockDim.x) {
-        uint32_t pw[3][2];
+        uint32_t pw[4][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          pw[0][h] = pw[1][h] = pw[2][h] = 0u;
+          pw[0][h] = pw[1][h] = pw[2][h] = pw[3][h] = 0u;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
             const int j = 8 * g + plane_dim(st.bits1, h, b);
-            const int v = j < d ? max(-8388607, min(8388607, __float2int_rn(qrow[j] * qinv))) : 0;
+            const int v = j < d ? max(-2147483647, __float2int_rn(ldexpf(qrow[j], -qe))) : 0;
             part += v;
             pw[0][h] |= (uint32_t)(v & 255) << (8 * b);
             pw[1][h] |= (uint32_t)((v >> 8) & 255) << (8 * b);
             pw[2][h] |= (uint32_t)((v >> 16) & 255) << (8 * b);
+            pw[3][h] |= (uint32_t)((v >> 24) & 255) << (8 * b);
           }
         }
 #pragma unroll
-        for (int pl = 0; pl < 3; ++pl) planes[pl * gpad + g] = make_uint2(pw[pl][0], pw[pl][1]);
+        for (int pl = 0; pl < 4; ++pl) planes[pl * gpad + g] = make_uint2(pw[pl][0], pw[pl][1]);
       }
       if (part != 0) atomicAdd(&qsum_int, (unsigned long long)part);
     }
@@ -556,24 +563,30 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
           load_consts(c_n, c_slot);
           // four accumulator sets (one per code group of a chunk, two chunks at
           // a time) keep the dp4a dependence chains short
-          GatherAcc A[4] = {{0u, 0u, 0}, {0u, 0u, 0}, {0u, 0u, 0}, {0u, 0u, 0}};
+          GatherAcc A[4] = {{0u, 0u, 0u, 0}, {0u, 0u, 0u, 0}, {0u, 0u, 0u, 0}, {0u, 0u, 0u, 0}};
           if (su != kNoSlot) {
             const uint4* row = reinterpret_cast<const uint4*>(slots + (size_t)(w * P + slot) * gg.slot_bytes +
                                                               (size_t)r * gg.stride);
+            auto lo2 = [](uint4 v) { return make_uint2(v.x, v.y); };
+            auto hi2 = [](uint4 v) { return make_uint2(v.z, v.w); };
             auto chunk4 = [&](const uint4 cw, int c) {
-              const uint4 a0 = pl4[2 * c], a1 = pl4[2 * c + 1];
-              const uint4 b0 = pl4[pstride4 + 2 * c], b1 = pl4[pstride4 + 2 * c + 1];
-              const uint4 c0 = pl4[2 * pstride4 + 2 * c], c1 = pl4[2 * pstride4 + 2 * c + 1];
-              group4(A[0], cw.x, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
-              group4(A[1], cw.y, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w), make_uint2(c0.z, c0.w));
-              group4(A[2], cw.z, make_uint2(a1.x, a1.y), make_uint2(b1.x, b1.y), make_uint2(c1.x, c1.y));
-              group4(A[3], cw.w, make_uint2(a1.z, a1.w), make_uint2(b1.z, b1.w), make_uint2(c1.z, c1.w));
+              uint4 p[4][2];
+#pragma unroll
+              for (int pl = 0; pl < 4; ++pl) {
+                p[pl][0] = pl4[pl * pstride4 + 2 * c];
+                p[pl][1] = pl4[pl * pstride4 + 2 * c + 1];
+              }
+              group4(A[0], cw.x, lo2(p[0][0]), lo2(p[1][0]), lo2(p[2][0]), lo2(p[3][0]));
+              group4(A[1], cw.y, hi2(p[0][0]), hi2(p[1][0]), hi2(p[2][0]), hi2(p[3][0]));
+              group4(A[2], cw.z, lo2(p[0][1]), lo2(p[1][1]), lo2(p[2][1]), lo2(p[3][1]));
+              group4(A[3], cw.w, hi2(p[0][1]), hi2(p[1][1]), hi2(p[2][1]), hi2(p[3][1]));
             };
             auto chunk8 = [&](const uint4 cw, int c, int h) {
-              const uint4 a0 = pl4[c], b0 = pl4[pstride4 + c], c0 = pl4[2 * pstride4 + c];
-              plane_step(A[2 * h], cw.x, cw.y, make_uint2(a0.x, a0.y), make_uint2(b0.x, b0.y), make_uint2(c0.x, c0.y));
-              plane_step(A[2 * h + 1], cw.z, cw.w, make_uint2(a0.z, a0.w), make_uint2(b0.z, b0.w),
-                         make_uint2(c0.z, c0.w));
+              uint4 p[4];
+#pragma unroll
+              for (int pl = 0; pl < 4; ++pl) p[pl] = pl4[pl * pstride4 + c];
+              plane_step(A[2 * h], cw.x, cw.y, lo2(p[0]), lo2(p[1]), lo2(p[2]), lo2(p[3]));
+              plane_step(A[2 * h + 1], cw.z, cw.w, hi2(p[0]), hi2(p[1]), hi2(p[2]), hi2(p[3]));
             };
             int c = l;
             for (; c + L < nchunks; c += 2 * L) {
@@ -597,6 +610,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
               A[0].a0 += A[i].a0;
               A[0].a1 += A[i].a1;
               A[0].a2 += A[i].a2;
+              A[0].a3 += A[i].a3;
             }
           }
           // the L lanes of a row are consecutive
@@ -604,9 +618,11 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
             A[0].a0 += __shfl_xor_sync(kFull, A[0].a0, o);
             A[0].a1 += __shfl_xor_sync(kFull, A[0].a1, o);
             A[0].a2 += __shfl_xor_sync(kFull, A[0].a2, o);
+            A[0].a3 += __shfl_xor_sync(kFull, A[0].a3, o);
           }
           if (l == 0 && live) {
-            const long long dot = (long long)A[0].a0 + ((long long)A[0].a1 << 8) + ((long long)A[0].a2 << 16) - qoff;
+            const long long dot = (long long)A[0].a0 + ((long long)A[0].a1 << 8) + ((long long)A[0].a2 << 16) +
+                                  ((long long)A[0].a3 << 24) - qoff;
             const float a = __fmul_rn(qscale, (float)dot);
             float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo), qs, cmq[m]));
             if (!ip) sc = __fadd_rn(__fadd_rn(qn, nrm), -2.0f * sc);
@@ -707,7 +723,7 @@ GatherGeom gather_geom(int row1, int d, int k) {
   const int r16 = row1 / 16;
   const int groups = (d + 7) / 8, gpad = (groups + 3) & ~3;
   (void)groups;
-  const size_t rest = (size_t)pow2_at_least(k + 2 * kGatherThreads) * 8 + (size_t)gpad * 3 * 8 + (size_t)(k + 2) * 4 + 16;
+  const size_t rest = (size_t)pow2_at_least(k + 2 * kGatherThreads) * 8 + (size_t)gpad * 4 * 8 + (size_t)(k + 2) * 4 + 16;
   GatherGeom g{};
   for (const size_t budget : {kGatherSmemBudget / 3 - 1024, kGatherSmemBudget / 2 - 1024, kGatherSmemBudget}) {
     for (int R = 32; R >= 1; R >>= 1) {

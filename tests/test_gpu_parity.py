@@ -293,6 +293,28 @@ def test_candidates_many_queries_per_block_and_limits():
     st.close()
 
 
+def test_candidates_adversarial_query_rounding():
+    """A query with one dominant element and every other element tiny and of
+    one sign, against vectors whose codes sit far from the code offset: the
+    case where rounding the query (the ID-gather first level's integer
+    products) errs most.  Scores stay within the float32 tolerance."""
+    d = 768
+    x = np.zeros((64, d), np.float32)
+    x[:, 0] = 15.0
+    x[1:, 1:] = np.random.default_rng(2).integers(0, 16, (63, d - 1)).astype(np.float32)
+    means = np.zeros((1, d), np.float32)
+    q = np.full((2, d), 3e-8, np.float32)
+    q[:, 0] = 1.0
+    q[1, 1:] = -3e-8
+    for metric in ("ip", "l2"):
+        st, ids = lib_store(x, means, 4, 8, metric)
+        enc = O.encode(x, means, 4, 8)
+        cand = np.tile(np.arange(64, dtype=np.int64), (2, 1))
+        gi, gs = st.search_candidates(torch.from_numpy(q).cuda(), torch.from_numpy(cand).cuda(), 10, 0)
+        check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP32)
+        st.close()
+
+
 def test_streaming_slots_match_the_replay():
     d, cap = 40, 5000
     mix = synth.Mixture(d=d, n_comp=8, sigma=0.3, seed=3)

@@ -96,3 +96,47 @@ def test_bench_aggregates_units_and_slowest_rank_over_gloo():
         p.join(60)
     assert all(p.exitcode == 0 for p in procs)
     assert out[0] == (300.0, 2.0) and out[1] == (300.0, 2.0)
+
+
+def test_fixed_point_query_error_bound():
+    """The ID-gather first level scales the float32 query by a power of two,
+    s = 2^(e - 30) with 2^e <= max|q| < 2^(e+1), rounds it once
+    (Q = rint(q / s), |Q| < 2^31) and multiplies Q with the codes exactly.
+    The change of <q, x^> (x^ = l + D c) is D sum_j (q_j - s Q_j)(c_j - off),
+    at most (s / 2) D sum_j |c_j - off|.  Checked in float64 on random,
+    spiky and adversarial cases (one dominant query element, every other
+    element's rounding error of one sign, codes far from their offset):
+    always below 5 % of the float32 tolerance 1e-5 ||q|| ||x^||."""
+    g = np.random.default_rng(3)
+    worst = 0.0
+    for d in (24, 96, 768, 4096):
+        for trial in range(40):
+            kind = trial % 4
+            if kind == 0:
+                q = g.standard_normal(d)
+            elif kind == 1:
+                q = g.standard_normal(d) * (g.random(d) < 0.02) + 1e-3 * g.standard_normal(d)
+            elif kind == 2:
+                q = np.full(d, 1.0) + 1e-6 * g.standard_normal(d)
+            else:
+                q = np.full(d, 0.3e-7)     # rounding errors all of one sign
+                q[0] = 1.0
+            q = q.astype(np.float32).astype(np.float64)
+            if kind == 3:
+                c = np.zeros(d)
+                c[0] = 15.0
+            else:
+                c = g.integers(0, 16, d).astype(np.float64)
+            lo, step = g.standard_normal(), abs(g.standard_normal()) + 1e-3
+            x = lo + step * c
+            s = 2.0 ** (np.floor(np.log2(np.abs(q).max())) - 30)
+            qq = np.rint(q / s)
+            assert np.abs(qq).max() < 2 ** 31
+            exact = q @ x
+            approx = (lo + 8 * step) * q.sum() + step * s * (qq @ (c - 8))
+            err = abs(approx - exact)
+            bound = (s / 2) * step * np.abs(c - 8).sum() * (1 + 1e-9) + 1e-12 * abs(exact)
+            assert err <= bound
+            tol = 1e-5 * np.linalg.norm(q) * np.linalg.norm(x)
+            worst = max(worst, err / tol)
+    assert worst < 0.05
