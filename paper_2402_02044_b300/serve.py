@@ -36,8 +36,9 @@ Model
 * Admission: each request holds device bytes (its inputs and outputs) while
   in flight; a request waits while the total would exceed the HBM budget,
   and one that could never fit is rejected.
-* Optional CUDA graphs: per lane and per power-of-two batch size, the search
-  of a padded batch is captured once and replayed.
+* Optional CUDA graphs: per lane, per power-of-two batch size and per
+  visibility bitmap (a graph keeps the bitmap it was captured with), the
+  search of a padded batch is captured once and replayed.
 """
 from __future__ import annotations
 
