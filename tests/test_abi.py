@@ -62,3 +62,18 @@ def test_null_arguments_are_rejected(lib):
     assert lib.lvq_create(None, None, None) == 1
     lib.lvq_destroy.argtypes = [ctypes.c_void_p]
     assert lib.lvq_destroy(None) == 1
+
+
+def test_snapshot_and_hold_calls_reject_null_handles(lib):
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.lvq_delete_hold.argtypes = [vp, vp, i64, vp, vp]
+    assert lib.lvq_delete_hold(None, None, 0, None, None) == 1
+    lib.lvq_release.argtypes = [vp, vp, i64, vp]
+    assert lib.lvq_release(None, None, 0, None) == 1
+    lib.lvq_live_words.argtypes = [vp, vp]
+    w = ctypes.c_int64(0)
+    assert lib.lvq_live_words(None, ctypes.byref(w)) == 1
+    lib.lvq_snapshot_live.argtypes = [vp, vp, vp]
+    assert lib.lvq_snapshot_live(None, None, None) == 1
+    lib.lvq_view_set_live.argtypes = [vp, vp]
+    assert lib.lvq_view_set_live(None, None) == 1
