@@ -46,6 +46,10 @@ UNIT = "distances/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one scan_mma launch over
 # 2M rows with the bench's 12,716-query mix (ncu --set full, B300)
 SCAN_MMA_DRAM_BYTES_2M = 1.934105e9 + 0.774121e9
+# DRAM bytes (read + write) of one ID-gather launch of 1,024 queries x 2,048
+# candidate ids, from an ncu capture of the same launch size at 2M rows (the
+# launch's traffic depends on the candidates, not on the rows)
+GATHER_DRAM_BYTES = 836.396e6 + 4.395e6
 
 
 def parse():
@@ -516,7 +520,8 @@ def main():
     g_bytes = nq_g * C * (384 + 4 + 4 + 1 + 8)
     gather_roof = {"kernel": "gather_kernel", "kernel_ms": g_ms, "algorithmic_bytes_per_launch": g_bytes,
                    "hbm_gbs": g_bytes / g_ms / 1e6 if g_ms else None, "peak_gbs": peaks.get("hbm_gbs"),
-                   "frac": g_bytes / g_ms / 1e6 / peaks["hbm_gbs"] if g_ms and peaks.get("hbm_gbs") else None}
+                   "frac": g_bytes / g_ms / 1e6 / peaks["hbm_gbs"] if g_ms and peaks.get("hbm_gbs") else None,
+                   "traffic": GATHER_DRAM_BYTES if (nq_g, C) == (1024, 2048) else None}
     roof["kernel"] = scan_kind
     roof["algorithmic_bytes_per_launch"] = bytes_per_launch
     roof["hbm_gbs_equiv"] = bytes_per_launch / per_launch_s / 1e9
