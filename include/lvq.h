@@ -88,6 +88,13 @@ typedef struct {
   int32_t mma_ctas;   /* persistent CTAs of the tensor-core scan (0 = one per SM) */
   int32_t fp32_q;     /* queries per CTA of the float32 scan: 1, 2, 4, 8 or 16 */
   int32_t fp32_splits;
+  /* Failure detection of the tensor-core scan: polls of each pipeline wait
+   * (a copy, an MMA or a partner role) before the scan gives up, records
+   * LVQ_ETIMEOUT in the store (lvq_last_error) and ends its CTAs; the
+   * results of that call are then undefined.  0 = the default, 2^24 polls
+   * (seconds).  The waits for a CTA's own copies and MMAs in flight before
+   * it exits always use the default, so no copy or MMA outlives the call. */
+  int32_t wait_polls;
 } lvq_tuning;
 
 /* Create an empty store on the current CUDA device.

@@ -40,7 +40,7 @@ __all__ = [
     "decode_second", "decode", "score", "best_first", "topk", "search_exhaustive",
     "search_candidates", "rerank", "ground_truth", "recall_at_k", "eps_first", "eps_second",
     "SlotReplay", "StoreFull", "pad_value", "take", "first_level_candidates",
-    "reconstruct_f32", "update_mean", "beam_search",
+    "reconstruct_f32", "update_mean", "beam_search", "exact_knn",
 ]
 
 
@@ -341,6 +341,25 @@ def ground_truth(enc: dict, means, q, k: int, metric: str, live=None, chunk: int
     return out_ids, out_s
 
 
+def exact_knn(x: np.ndarray, q, k: int, metric: str, chunk: int = 1 << 16):
+    """Exact k-NN of the raw (unquantised) float32 vectors x: the k best rows
+    by (score, id) with scores in float64 (the k-NN problem of Sec. 2.1, on
+    the original data).  Returns (ids int64 [nq, k], scores float64 [nq, k])."""
+    x = np.asarray(x, dtype=F32)
+    q = np.atleast_2d(np.asarray(q, dtype=F32))
+    best_ids = [np.empty(0, np.int64) for _ in range(len(q))]
+    best_s = [np.empty(0, F64) for _ in range(len(q))]
+    for s in range(0, len(x), chunk):
+        rows = np.arange(s, min(len(x), s + chunk), dtype=np.int64)
+        sc = score(q, x[s:s + chunk].astype(F64), metric)
+        for i in range(len(q)):
+            all_ids = np.concatenate([best_ids[i], rows])
+            all_s = np.concatenate([best_s[i], sc[i]])
+            order = best_first(all_s, all_ids, metric)[:k]
+            best_ids[i], best_s[i] = all_ids[order], all_s[order]
+    return np.stack(best_ids), np.stack(best_s)
+
+
 def recall_at_k(found: np.ndarray, truth: np.ndarray, k: int) -> float:
     """k-recall@k = |S cap G| / k averaged over queries (Sec. 2.1)."""
     found = np.atleast_2d(found)[:, :k]
@@ -395,24 +414,41 @@ def update_mean(enc: dict, means, m: int, new_mean, live=None):
 # Greedy beam search over a graph (Alg. 1), first-level scores
 # --------------------------------------------------------------------------
 
-def beam_search(enc: dict, means, q, graph, starts, L: int, k: int, metric: str, live=None, max_expand=None):
+def beam_search(enc: dict, means, q, graph, starts, L: int, k: int, metric: str, live=None, max_expand=None,
+                tol=None):
     """Alg. 1 for each query: a search list of at most L nodes ordered by
     (first-level score, id), seeded with ``starts``; repeatedly expand the
     best node not yet expanded (score its out-neighbours not seen before and
     keep the L best of the list) until every listed node is expanded or
     ``max_expand`` expansions were made.  Deleted nodes are never listed.
     Returns the k best listed (ids int64 [nq, k], scores float64 [nq, k],
-    padded with -1 / pad_value)."""
+    padded with -1 / pad_value).
+
+    With ``tol`` given, a third array flags, per query, whether a decision
+    of the search rested on two scores a and b with
+    |s_a - s_b| <= tol * (scale_a + scale_b), scale = max(|s|, ||q|| ||x^||):
+    scores each known only to within tol * scale (a float32 search) may
+    order such a pair either way.  The decisions are the node expanded next
+    (the best unexpanded node against the next one) and the cut of the list
+    to L nodes (its L-th node against the (L+1)-th).  The final choice of
+    the k best is not flagged: it is compared with ties allowed."""
     q = np.atleast_2d(np.asarray(q, dtype=F32))
     graph = np.asarray(graph)
     n = len(enc["lower"])
     live = np.ones(n, dtype=bool) if live is None else np.asarray(live, dtype=bool)
     xh = decode_first(enc, means)
+    xn = np.linalg.norm(xh, axis=1)
     out_ids = np.full((len(q), k), -1, dtype=np.int64)
     out_s = np.full((len(q), k), pad_value(metric), dtype=F64)
+    ambiguous = np.zeros(len(q), dtype=bool)
     key = (lambda s: s) if metric == L2 else (lambda s: -s)
     for i in range(len(q)):
         sc = score(q[i], xh, metric)[0]
+        scl = np.maximum(np.abs(sc), float(np.linalg.norm(q[i].astype(F64))) * xn)
+
+        def close(a, b):
+            return tol is not None and abs(sc[a] - sc[b]) <= tol * (scl[a] + scl[b])
+
         seen = set()
         lst = []                      # (key, id)
         for s in starts:
@@ -420,13 +456,19 @@ def beam_search(enc: dict, means, q, graph, starts, L: int, k: int, metric: str,
             if 0 <= s < n and live[s] and s not in seen:
                 seen.add(s)
                 lst.append((key(sc[s]), s))
-        lst = sorted(lst)[:L]
+        lst = sorted(lst)
+        if len(lst) > L and close(lst[L - 1][1], lst[L][1]):
+            ambiguous[i] = True
+        lst = lst[:L]
         expanded = set()
         steps = 0
         while max_expand is None or steps < max_expand:
-            nxt = next((v for v in lst if v[1] not in expanded), None)
-            if nxt is None:
+            todo = [v for v in lst if v[1] not in expanded]
+            if not todo:
                 break
+            nxt = todo[0]
+            if len(todo) > 1 and close(nxt[1], todo[1][1]):
+                ambiguous[i] = True
             expanded.add(nxt[1])
             steps += 1
             for u in graph[nxt[1]]:
@@ -435,10 +477,15 @@ def beam_search(enc: dict, means, q, graph, starts, L: int, k: int, metric: str,
                     continue
                 seen.add(u)
                 lst.append((key(sc[u]), u))
-            lst = sorted(lst)[:L]
+            lst = sorted(lst)
+            if len(lst) > L and close(lst[L - 1][1], lst[L][1]):
+                ambiguous[i] = True
+            lst = lst[:L]
         top = lst[:k]
         out_ids[i, :len(top)] = [u for _, u in top]
         out_s[i, :len(top)] = [sc[u] for _, u in top]
+    if tol is not None:
+        return out_ids, out_s, ambiguous
     return out_ids, out_s
 
 

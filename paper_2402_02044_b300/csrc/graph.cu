@@ -1,7 +1,9 @@
 // Greedy beam search over a graph (Alg. 1), one CTA per query.
 //
-// The search list holds at most L keys (first-level score, id) sorted in
-// shared memory; bit 31 of a key's id word marks a node already expanded.
+// The search list holds at most L keys sorted in shared memory: the
+// first-level score in the high word and (id << 1 | expanded) in the low
+// word, so that equal scores order by id whether or not a node has been
+// expanded (ids are below 2^31).  The k1 best leave as plain (score, id) keys.
 // Each step expands the best listed node not yet expanded: its out-
 // neighbours that are live and not seen before (an open-addressing set in
 // shared memory) are scored with the first level in float32, one warp per
@@ -17,7 +19,7 @@ namespace lvq {
 namespace {
 
 constexpr int kBeamThreads = 256;
-constexpr uint32_t kExpanded = 0x80000000u;
+constexpr uint32_t kExpanded = 1u;  // low bit of a list key's id word
 
 // First-level float32 score of slot s by one warp (valid in every lane):
 // x1_j = mu_mj + l + D c_j; L2: sum (q_j - x1_j)^2, IP: sum q_j x1_j.
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(DeviceStore st, cons
     take = __shfl_sync(kFull, take, 0);
     if (take) {
       const float sc = score1_warp(st, s, qsh);
-      if (lane == 0) list[atomicAdd(&nnew, 1)] = make_key(sc, (uint32_t)s, st.metric);
+      if (lane == 0) list[atomicAdd(&nnew, 1)] = make_key(sc, (uint32_t)s << 1, st.metric);
     }
   }
   __syncthreads();
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(DeviceStore st, cons
     }
     __syncthreads();
     if (sel < 0) break;
-    const int node = (int)((uint32_t)list[sel] & ~kExpanded);
+    const int node = (int)((uint32_t)list[sel] >> 1);
     const int32_t* nb = graph + (int64_t)node * R;
     for (int r = warp; r < R; r += nw) {
       const int u = nb[r];
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(DeviceStore st, cons
       take = __shfl_sync(kFull, take, 0);
       if (take) {
         const float sc = score1_warp(st, u, qsh);
-        if (lane == 0) list[L + atomicAdd(&nnew, 1)] = make_key(sc, (uint32_t)u, st.metric);
+        if (lane == 0) list[L + atomicAdd(&nnew, 1)] = make_key(sc, (uint32_t)u << 1, st.metric);
       }
     }
     __syncthreads();
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(DeviceStore st, cons
   uint64_t* dst = out + (int64_t)qi * k1;
   for (int i = threadIdx.x; i < k1; i += blockDim.x) {
     uint64_t v = i < cnt ? list[i] : kNoKey;
-    if (v != kNoKey) v &= ~(uint64_t)kExpanded;
+    if (v != kNoKey) v = (v & 0xFFFFFFFF00000000ull) | ((uint32_t)v >> 1);
     dst[i] = v;
   }
 }
@@ -186,12 +188,11 @@ cudaError_t launch_beam(const DeviceStore& st, const float* q, int64_t nq, const
   if (nq <= 0) return cudaSuccess;
   const int H = beam_set_slots(n_starts, R, max_expand);
   const size_t sm = beam_smem(st, L, R, H);
-  static bool attr = false;
-  if (!attr) {
-    // the kernel also has a few bytes of static shared memory
-    const cudaError_t e = cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  // the kernel also has a few bytes of static shared memory
+  static std::atomic<uint64_t> attr{0};
+  {
+    const cudaError_t ea = max_dyn_smem_once((const void*)beam_kernel, 220 * 1024, attr);
+    if (ea != cudaSuccess) return ea;
   }
   beam_kernel<<<(unsigned)nq, kBeamThreads, sm, stream>>>(st, q, graph, n_graph, R, starts, n_starts, L, max_expand,
                                                           H, k1, keys);

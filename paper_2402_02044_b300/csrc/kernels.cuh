@@ -73,6 +73,7 @@ struct ScanPlan {
   int grid;             // persistent CTAs
   int* counts = nullptr;  // [nq][splits] valid keys per list (null: lists padded with kNoKey)
   uint64_t* gthr = nullptr;  // [nq] per-query bound shared by the CTAs of the tensor-core scan
+  uint32_t wait_polls = 0;   // polls of each pipeline wait of the tensor-core scan (0: the default)
 };
 constexpr int kMaxMergeLists = 1024;  // lists per query when counts are given
 

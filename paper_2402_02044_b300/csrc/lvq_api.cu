@@ -5,6 +5,8 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 #include "topk.cuh"
 
@@ -13,6 +15,14 @@ using namespace lvq;
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// An NVTX range around the host side of one C-ABI call (the launches it
+// enqueues), named after the entry point, for timelines in profilers.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+#define LVQ_RANGE() NvtxRange nvtx_range_(__func__)
 constexpr int64_t kReencodeChunk = 65536;  // rows reconstructed and re-encoded per pass
 
 // counters block layout (device, int64 words)
@@ -107,7 +117,9 @@ struct ScanScratch {
   void* small = nullptr;  // rounded queries of the small-batch scan
 };
 
-size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, ScanScratch* out) {
+// n_rows: the rows to scan (a snapshot of the store's row bound, taken once
+// per call so that the sizing and the layout of a plan always agree).
+size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, int64_t n_rows, void* base, ScanScratch* out) {
   const DeviceStore& st = s->ds;
   const bool mma = path == kPathMma;
   Carver c(base);
@@ -120,7 +132,6 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, S
   sc.prep.q16sum = nullptr;
   sc.prep.nq_pad = nq;
   sc.prep.kq = 0;
-  const int64_t n_rows = root_of(s)->rows_bound.load();
   int grid, tiles_rows;
   int64_t groups;
   if (mma) {
@@ -166,6 +177,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, void* base, S
     sc.plan.grid = (int)(groups * splits < grid ? groups * splits : grid);
   }
   sc.plan.splits = splits;
+  sc.plan.wait_polls = (uint32_t)s->tuning.wait_polls;
   sc.plan.n_rows = n_rows;
   sc.plan.k1 = k1;
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
@@ -226,11 +238,12 @@ lvq_status first_level(lvq_store* s, const float* q, int64_t nq, int k1, int k, 
     return fail(s, LVQ_EINVAL, "unknown precision");
   }
   std::lock_guard<std::mutex> g(s->mu);
-  const size_t need = plan_scan(s, nq, k1, path, nullptr, nullptr);
+  const int64_t n_rows = root_of(s)->rows_bound.load();
+  const size_t need = plan_scan(s, nq, k1, path, n_rows, nullptr, nullptr);
   lvq_status rc = ensure_ws(s, need);
   if (rc != LVQ_OK) return rc;
   ScanScratch sc;
-  plan_scan(s, nq, k1, path, s->ws, &sc);
+  plan_scan(s, nq, k1, path, n_rows, s->ws, &sc);
   cudaError_t e;
   {
     Prof p(s, stream, LVQ_K_PREP, path == kPathSmall ? 2 : 1);
@@ -383,6 +396,7 @@ lvq_status lvq_store_view(const lvq_store* base, lvq_store** out) {
 
 lvq_status lvq_encode(const lvq_store* s, const float* x, int64_t n, uint8_t* codes1, uint8_t* codes2,
                       float* lower, float* step, uint8_t* mean_id, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (n == 0) return LVQ_OK;
@@ -401,6 +415,7 @@ lvq_status lvq_encode(const lvq_store* s, const float* x, int64_t n, uint8_t* co
 
 static lvq_status insert_impl(lvq_store* s, const float* x, int64_t n, int64_t* out_ids, lvq_stream_t stream,
                               bool deferred) {
+  NvtxRange nvtx_range_(deferred ? "lvq_insert_deferred" : "lvq_insert");
   if (!s) return LVQ_EINVAL;
   if (n < 0 || n > s->ds.capacity) return fail(s, LVQ_EINVAL, "n out of range");
   if (n == 0) return LVQ_OK;
@@ -438,6 +453,7 @@ lvq_status lvq_insert_deferred(lvq_store* s, const float* x, int64_t n, int64_t*
 }
 
 lvq_status lvq_publish(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (n == 0) return LVQ_OK;
@@ -450,6 +466,7 @@ lvq_status lvq_publish(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t
 }
 
 lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_n_deleted, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (!out_n_deleted || (n > 0 && !ids)) return fail(s, LVQ_EINVAL, "null pointer");
@@ -466,6 +483,7 @@ lvq_status lvq_delete(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_
 
 lvq_status lvq_delete_hold(lvq_store* s, const int64_t* ids, int64_t n, int64_t* out_n_deleted,
                            lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (!out_n_deleted || (n > 0 && !ids)) return fail(s, LVQ_EINVAL, "null pointer");
@@ -481,6 +499,7 @@ lvq_status lvq_delete_hold(lvq_store* s, const int64_t* ids, int64_t n, int64_t*
 }
 
 lvq_status lvq_release(lvq_store* s, const int64_t* ids, int64_t n, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (n > 0 && !ids) return fail(s, LVQ_EINVAL, "null pointer");
@@ -496,6 +515,7 @@ lvq_status lvq_live_words(const lvq_store* s, int64_t* out_words) {
 }
 
 lvq_status lvq_snapshot_live(const lvq_store* s, uint32_t* dst, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   lvq_store* m = const_cast<lvq_store*>(s);
   if (!dst) return fail(m, LVQ_EINVAL, "null pointer");
@@ -517,6 +537,7 @@ lvq_status lvq_view_set_live(lvq_store* view, const uint32_t* live) {
 }
 
 lvq_status lvq_update_mean(lvq_store* s, int32_t m, const float* new_mean, int64_t* out_count, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (!new_mean || !out_count) return fail(s, LVQ_EINVAL, "null pointer");
   if (m < 0 || m >= s->ds.n_means) return fail(s, LVQ_EINVAL, "mean index out of range");
@@ -562,6 +583,7 @@ lvq_status lvq_update_mean(lvq_store* s, int32_t m, const float* new_mean, int64
 lvq_status lvq_search_graph(const lvq_store* cs, const float* q, int64_t nq, const int32_t* graph, int64_t n_graph,
                             int32_t R, const int64_t* starts, int32_t n_starts, int32_t L, int32_t max_expand,
                             int32_t k1, int32_t k, int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -605,6 +627,7 @@ lvq_status lvq_search_graph(const lvq_store* cs, const float* q, int64_t nq, con
 
 lvq_status lvq_search_exhaustive(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t k,
                                  int32_t precision, int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -618,6 +641,7 @@ lvq_status lvq_search_exhaustive(const lvq_store* cs, const float* q, int64_t nq
 
 lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t k,
                                         int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -645,7 +669,10 @@ lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int
     base = g_static_addr[s->device];
   }
   std::lock_guard<std::mutex> g(s->mu);
-  const size_t need = plan_scan(s, nq, kk1, kPathSmall, nullptr, nullptr);
+  // one snapshot of the row bound sizes and lays out the plan: an insert on
+  // another thread cannot enlarge it between the check and the launch
+  const int64_t n_rows = root_of(s)->rows_bound.load();
+  const size_t need = plan_scan(s, nq, kk1, kPathSmall, n_rows, nullptr, nullptr);
   if (need > kStaticScratchBytes) {
     char msg[160];
     snprintf(msg, sizeof msg, "lvq_search_exhaustive_static: plan needs %zu bytes of scratch, the static array holds %zu",
@@ -653,7 +680,7 @@ lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int
     return fail(s, LVQ_EINVAL, msg);
   }
   ScanScratch sc;
-  plan_scan(s, nq, kk1, kPathSmall, base, &sc);
+  plan_scan(s, nq, kk1, kPathSmall, n_rows, base, &sc);
   const cudaStream_t str = (cudaStream_t)stream;
   cudaError_t e = launch_prep_queries(st, q, nq, sc.prep, str);
   if (e == cudaSuccess) e = launch_small_prep(st, q, nq, sc.small, str);
@@ -668,6 +695,7 @@ lvq_status lvq_search_exhaustive_static(const lvq_store* cs, const float* q, int
 
 lvq_status lvq_search_first_level(const lvq_store* cs, const float* q, int64_t nq, int32_t k1, int32_t precision,
                                   int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -680,6 +708,7 @@ lvq_status lvq_search_first_level(const lvq_store* cs, const float* q, int64_t n
 lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq, const int64_t* cand,
                                  int32_t n_cand, int32_t k1, int32_t k, int64_t* out_ids, float* out_scores,
                                  lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -735,6 +764,7 @@ lvq_status lvq_search_candidates(const lvq_store* cs, const float* q, int64_t nq
 
 lvq_status lvq_rerank(const lvq_store* cs, const float* q, int64_t nq, const int64_t* ids, int32_t k1, int32_t k,
                       int64_t* out_ids, float* out_scores, lvq_stream_t stream) {
+  LVQ_RANGE();
   lvq_status rc = check_q(cs, q, nq);
   if (rc != LVQ_OK) return rc;
   lvq_store* s = const_cast<lvq_store*>(cs);
@@ -750,6 +780,7 @@ lvq_status lvq_rerank(const lvq_store* cs, const float* q, int64_t nq, const int
 
 lvq_status lvq_export(const lvq_store* s, const int64_t* ids, int64_t n, uint8_t* codes1, uint8_t* codes2,
                       float* lower, float* step, uint8_t* mean_id, lvq_stream_t stream) {
+  LVQ_RANGE();
   if (!s) return LVQ_EINVAL;
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (n == 0) return LVQ_OK;
@@ -778,14 +809,16 @@ lvq_status lvq_reserve(lvq_store* s, int64_t max_nq, int32_t max_k1, int32_t max
   if (!s || max_nq < 0 || max_k1 < 1 || max_k1 > kMaxK1 || max_cand < 0) return LVQ_EINVAL;
   (void)max_cand;
   std::lock_guard<std::mutex> g(s->mu);
-  size_t need = plan_scan(s, max_nq, max_k1, kPathFp32, nullptr, nullptr);
+  // sized for a full store: later inserts cannot outgrow the reservation
+  const int64_t n_rows = s->ds.capacity;
+  size_t need = plan_scan(s, max_nq, max_k1, kPathFp32, n_rows, nullptr, nullptr);
   if (mma_supported(s->ds)) {
-    const size_t m = plan_scan(s, max_nq, max_k1, kPathMma, nullptr, nullptr);
+    const size_t m = plan_scan(s, max_nq, max_k1, kPathMma, n_rows, nullptr, nullptr);
     if (m > need) need = m;
   }
   const int64_t small_nq = max_nq < kSmallMaxQ ? max_nq : kSmallMaxQ;
   if (small_supported(s->ds, small_nq, max_k1)) {
-    const size_t m = plan_scan(s, small_nq, max_k1, kPathSmall, nullptr, nullptr);
+    const size_t m = plan_scan(s, small_nq, max_k1, kPathSmall, n_rows, nullptr, nullptr);
     if (m > need) need = m;
   }
   return ensure_ws(s, need);
@@ -796,7 +829,7 @@ lvq_status lvq_set_tuning(lvq_store* s, const lvq_tuning* t) {
   if (t->mma_n != 0 && t->mma_n != 16 && t->mma_n != 32 && t->mma_n != 64 && t->mma_n != 128) return LVQ_EINVAL;
   if (t->fp32_q != 0 && t->fp32_q != 1 && t->fp32_q != 2 && t->fp32_q != 4 && t->fp32_q != 8 && t->fp32_q != 16)
     return LVQ_EINVAL;
-  if (t->mma_ctas < 0 || t->fp32_splits < 0) return LVQ_EINVAL;
+  if (t->mma_ctas < 0 || t->fp32_splits < 0 || t->wait_polls < 0) return LVQ_EINVAL;
   std::lock_guard<std::mutex> g(s->mu);
   s->tuning = *t;
   return LVQ_OK;

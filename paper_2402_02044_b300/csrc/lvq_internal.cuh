@@ -96,6 +96,20 @@ struct lvq_store {
 namespace lvq {
 
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Raises a kernel's dynamic shared memory limit on the current device, once
+// per device: `done` (one per kernel) keeps a bit per device ordinal below
+// 64 (the attribute is per device); on higher ordinals it is set every call.
+inline cudaError_t max_dyn_smem_once(const void* func, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Ordering of results: an unsigned 64-bit key whose high word is the score

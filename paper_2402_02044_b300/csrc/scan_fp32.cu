@@ -170,11 +170,9 @@ __global__ void __launch_bounds__(kThreads) scan_fp32_kernel(Fp32Args a) {
 
 template <int QB, int BITS>
 cudaError_t launch_t(const Fp32Args& a, size_t smem, int grid, cudaStream_t stream) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(scan_fp32_kernel<QB, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = max_dyn_smem_once((const void*)scan_fp32_kernel<QB, BITS>, 160 * 1024, attr);
+  if (e != cudaSuccess) return e;
   scan_fp32_kernel<QB, BITS><<<grid, kThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }

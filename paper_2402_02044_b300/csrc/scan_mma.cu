@@ -78,6 +78,7 @@ struct MmaArgs {
   int64_t groups;     // query tiles
   int segs;           // database segments (equal ranges of tiles)
   int64_t jobs;       // groups x segs; job j = (query tile j % groups, segment j / groups)
+  uint32_t wait_limit;  // polls of a pipeline wait before the CTA gives up (drains use kWaitLimit)
 };
 
 struct Smem {
@@ -180,7 +181,7 @@ struct Ctx {
 // jump to the role's exit (a label `out` in the calling function).
 #define LVQ_WAIT(c, bar, par)                            \
   do {                                                   \
-    if (!mbar_wait((bar), (par), kWaitLimit)) {          \
+    if (!mbar_wait((bar), (par), a.wait_limit)) {        \
       *(c).abort_sh = 1;                                 \
       set_error(a.st.err, LVQ_ETIMEOUT);                 \
       goto out;                                          \
@@ -423,7 +424,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
     for (int64_t t = t0; t < t1; ++t) {
       const int db = di & 1;
       if (ew == 0) {
-        const bool ok = !*c.abort_sh && mbar_wait(c.B.d_full + db, (di >> 1) & 1, kWaitLimit);
+        const bool ok = !*c.abort_sh && mbar_wait(c.B.d_full + db, (di >> 1) & 1, a.wait_limit);
         if (!ok && lane == 0) {
           if (!*c.abort_sh) set_error(st.err, LVQ_ETIMEOUT);
           *c.abort_sh = 1;
@@ -630,17 +631,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---- host side -------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once per process (thread-safe initialisation of a local static)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -666,13 +666,9 @@ int max_n_tile(const DeviceStore& st) {
 template <int N, int BITS, int CM>
 cudaError_t launch_nbc(const CUtensorMap& cm, const CUtensorMap& qm, const MmaArgs& a, int grid, size_t smem,
                        cudaStream_t stream) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(scan_mma_kernel<N, BITS, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         232448);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = max_dyn_smem_once((const void*)scan_mma_kernel<N, BITS, CM>, 232448, attr);
+  if (e != cudaSuccess) return e;
   scan_mma_kernel<N, BITS, CM><<<grid, kThreads, smem, stream>>>(cm, qm, a);
   return cudaGetLastError();
 }
@@ -758,6 +754,7 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   a.jobs = a.groups * a.segs;
   a.counts = plan.counts;
   a.gthr = plan.gthr;
+  a.wait_limit = plan.wait_polls > 0 ? plan.wait_polls : kWaitLimit;
   if (!a.counts || !a.gthr || a.segs < 1 || a.segs > a.ntiles) return cudaErrorInvalidValue;
   const int grid = plan.grid;
 

@@ -422,13 +422,9 @@ __global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const f
 
 template <int QB, int BITS, int G>
 cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_t smem, cudaStream_t stream) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(scan_small_kernel<QB, BITS, G>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = max_dyn_smem_once((const void*)scan_small_kernel<QB, BITS, G>, kSmemLimit, attr);
+  if (e != cudaSuccess) return e;
   scan_small_kernel<QB, BITS, G><<<grid, small_threads(G), smem, stream>>>(cm, a);
   return cudaGetLastError();
 }

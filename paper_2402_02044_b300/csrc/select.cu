@@ -109,7 +109,8 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
 #pragma unroll
     for (int u = 0; u < kRU; ++u) {
       const uint64_t key = i0 + u < n ? keys[i0 + u] : kNoKey;
-      ok[u] = key != kNoKey;
+      // ids past the store are skipped (only a scan that gave up leaves any)
+      ok[u] = key != kNoKey && (int64_t)(uint32_t)key < st.capacity;
       sid[u] = (uint32_t)key;
     }
     // per-candidate constants, one lane each
@@ -117,7 +118,7 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
     int m_l = 0;
     {
       const uint64_t key = (lane < kRU && i0 + lane < n) ? keys[i0 + lane] : kNoKey;
-      if (key != kNoKey) {
+      if (key != kNoKey && (int64_t)(uint32_t)key < st.capacity) {
         const uint32_t sl = (uint32_t)key;
         lo_l = __ldg(st.lower + sl);
         st_l = __ldg(st.step + sl);
@@ -231,7 +232,10 @@ __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const f
     int run = 0;
     for (int c0 = 0; c0 < splits; c0 += T) {
       const int i = c0 + threadIdx.x;
-      const int v = i < splits ? counts[(int64_t)qi * splits + i] : 0;
+      // a list holds at most k1 keys; the clamp keeps a scan that gave up
+      // (LVQ_ETIMEOUT, lists left unwritten) from sending the merge past them
+      int v = i < splits ? counts[(int64_t)qi * splits + i] : 0;
+      v = v < 0 ? 0 : v > k1 ? k1 : v;
       int sum;
       const int at = run + block_exclusive_scan(v, scan_sh, sum);
       if (i < splits) start[i] = at;
@@ -672,11 +676,9 @@ template <int T>
 cudaError_t launch_merge_t(const DeviceStore& st, const float* q, int64_t nq, const uint64_t* partial,
                            const int* counts, int splits, int k1, int k, bool rerank, int64_t* out_ids,
                            float* out_scores, size_t sm, cudaStream_t stream) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(merge_rerank_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = max_dyn_smem_once((const void*)merge_rerank_kernel<T>, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   merge_rerank_kernel<T><<<(unsigned)nq, T, sm, stream>>>(st, q, partial, counts, splits, k1, k, rerank ? 1 : 0,
                                                           out_ids, out_scores);
   return cudaGetLastError();
@@ -703,11 +705,9 @@ cudaError_t launch_rerank(const DeviceStore& st, const float* q, int64_t nq, con
                           int k1, int k, int64_t* out_ids, float* out_scores, cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
   const size_t sm = (size_t)pow2_at_least(k1) * 16 + (size_t)st.d * 4 + (size_t)(k + 2) * 4 + 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = max_dyn_smem_once((const void*)rerank_kernel, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
   rerank_kernel<<<(unsigned)nq, kRerankThreads, sm, stream>>>(st, q, ids, k1, k, out_ids, out_scores);
   return cudaGetLastError();
 }
@@ -751,12 +751,10 @@ cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, con
   if (nq <= 0) return cudaSuccess;
   const GatherGeom g = gather_geom(st.row1, st.d, k);
   if (g.smem > kGatherSmemBudget) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kGatherSmemBudget);
+  static std::atomic<uint64_t> attr{0};
+  {
+    const cudaError_t e = max_dyn_smem_once((const void*)gather_kernel, (int)kGatherSmemBudget, attr);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);

@@ -35,7 +35,7 @@ class lvq_config(ctypes.Structure):
 
 class lvq_tuning(ctypes.Structure):
     _fields_ = [("mma_n", ctypes.c_int32), ("mma_ctas", ctypes.c_int32), ("fp32_q", ctypes.c_int32),
-                ("fp32_splits", ctypes.c_int32)]
+                ("fp32_splits", ctypes.c_int32), ("wait_polls", ctypes.c_int32)]
 
 
 class LVQError(RuntimeError):
@@ -272,15 +272,16 @@ def lvq_reserve(store, max_nq: int, max_k1: int, max_cand: int = 0):
     _check(load().lvq_reserve(store, max_nq, max_k1, max_cand), "lvq_reserve")
 
 
-def lvq_set_tuning(store, mma_n=0, mma_ctas=0, fp32_q=0, fp32_splits=0):
-    t = lvq_tuning(mma_n, mma_ctas, fp32_q, fp32_splits)
+def lvq_set_tuning(store, mma_n=0, mma_ctas=0, fp32_q=0, fp32_splits=0, wait_polls=0):
+    t = lvq_tuning(mma_n, mma_ctas, fp32_q, fp32_splits, wait_polls)
     _check(load().lvq_set_tuning(store, ctypes.byref(t)), "lvq_set_tuning")
 
 
 def lvq_get_tuning(store) -> dict:
     t = lvq_tuning()
     _check(load().lvq_get_tuning(store, ctypes.byref(t)), "lvq_get_tuning")
-    return dict(mma_n=t.mma_n, mma_ctas=t.mma_ctas, fp32_q=t.fp32_q, fp32_splits=t.fp32_splits)
+    return dict(mma_n=t.mma_n, mma_ctas=t.mma_ctas, fp32_q=t.fp32_q, fp32_splits=t.fp32_splits,
+                wait_polls=t.wait_polls)
 
 
 def lvq_profile_enable(store, on: bool = True):

@@ -16,7 +16,8 @@ float32 vectors:
   are inserted afresh with that mean ("fresh").
 
 Encoding, search and the centre update run in the library's kernels; the
-error and the ground truth are measurement, computed with torch on the GPU.
+error and the ground truth are measurement, computed with torch on the GPU
+in float64 (the exact k-NN of the raw vectors, ties to the lower id).
 Run: python -m paper_2402_02044_b300.robustness [--n N] [--d D].
 """
 from __future__ import annotations
@@ -32,21 +33,87 @@ import synth
 from .lvq import Store
 
 
-def _eps1(st: Store, x: torch.Tensor, ids: torch.Tensor, means: torch.Tensor) -> float:
+def eps1_per_vector(st: Store, x: torch.Tensor, ids: torch.Tensor, means: torch.Tensor) -> float:
+    """First-level quantisation error (Eq. 5) divided by the number of vectors:
+    mean over rows of ||x - mu_m - (l + D c)||^2 from the stored records,
+    summed in float64."""
     e = st.export(ids)
-    xh = means[e["mean_id"].long()] + e["lower"][:, None] + e["step"][:, None] * e["codes1"].float()
-    return float(((x - xh).double() ** 2).sum(1).mean())
+    xh = means[e["mean_id"].long()].double() + e["lower"].double()[:, None] + \
+        e["step"].double()[:, None] * e["codes1"].double()
+    return float(((x.double() - xh) ** 2).sum(1).mean())
+
+
+def raw_truth(x: torch.Tensor, q: torch.Tensor, metric: str, k: int = 10) -> torch.Tensor:
+    """Ids of the exact k nearest raw vectors of each query, scored in
+    float64 and ordered by (score, id)."""
+    xd, qd = x.double(), q.double()
+    if metric == "ip":
+        key = -(qd @ xd.T)
+    else:
+        key = (qd * qd).sum(1, keepdim=True) - 2 * qd @ xd.T + (xd * xd).sum(1)[None]
+    # stable sort: equal scores keep ascending id order
+    return torch.sort(key, dim=1, stable=True).indices[:, :k]
+
+
+def decoded_truth(st: Store, q: torch.Tensor, k: int = 10, level: int = 2, n_rows: int = None,
+                  chunk: int = 1 << 20) -> torch.Tensor:
+    """Ids of the exact k best live slots of each query by the score of the
+    decoded vectors at ``level`` (2: both levels), in float64 and ordered by
+    (score, id): the ground truth of recall@k for the store's own search.
+    The records are read back with lvq_export and decoded with torch in
+    float64 (x^ = mu_m + l + D c [+ l2 + D2 c2]), ``chunk`` slots at a time;
+    ``n_rows`` bounds the slots visited (default: the store's capacity)."""
+    n = st.capacity if n_rows is None else n_rows
+    means = torch.from_numpy(st.means).cuda().double()
+    qd = q.double()
+    ip = st.metric == "ip"
+    best_key = torch.full((len(q), 0), 0.0, dtype=torch.float64, device=q.device)
+    best_id = torch.full((len(q), 0), 0, dtype=torch.int64, device=q.device)
+    live_bits = st.live_snapshot()
+    torch.cuda.synchronize()
+    for s in range(0, n, chunk):
+        ids = torch.arange(s, min(n, s + chunk), device=q.device)
+        w = live_bits[ids >> 5].long() & 0xFFFFFFFF
+        alive = ((w >> (ids & 31)) & 1).bool()
+        ids = ids[alive]
+        if len(ids) == 0:
+            continue
+        e = st.export(ids)
+        x = means[e["mean_id"].long()] + e["lower"].double()[:, None] + e["step"].double()[:, None] * e["codes1"].double()
+        if level == 2 and st.bits2:
+            step = e["step"]
+            lower2 = (-step * 0.5).double()  # exact halving
+            step2 = (step / 255.0).double()   # D2 = fl32(D / 255), the residual grid
+            x = x + lower2[:, None] + step2[:, None] * e["codes2"].double()
+        if ip:
+            key = -(qd @ x.T)
+        else:
+            key = (qd * qd).sum(1, keepdim=True) - 2 * qd @ x.T + (x * x).sum(1)[None]
+        kk = min(k + 8, key.shape[1])
+        top = torch.topk(key, kk, dim=1, largest=False)
+        best_key = torch.cat([best_key, top.values], 1)
+        best_id = torch.cat([best_id, ids[top.indices]], 1)
+        # keep the k + 8 best so far by (score, id)
+        order = torch.argsort(best_id, dim=1, stable=True)
+        bk, bi = best_key.gather(1, order), best_id.gather(1, order)
+        order = torch.argsort(bk, dim=1, stable=True)[:, :k + 8]
+        best_key, best_id = bk.gather(1, order), bi.gather(1, order)
+    return best_id[:, :k]
+
+
+def recall(found: torch.Tensor, truth: torch.Tensor, k: int = 10) -> float:
+    """k-recall@k (Sec. 2.1): |found cap truth| / k averaged over queries."""
+    hits = sum(len(set(a[a >= 0].tolist()) & set(b.tolist())) for a, b in zip(found[:, :k].cpu(), truth[:, :k].cpu()))
+    return hits / (float(k) * len(found))
 
 
 def _recall(st: Store, x: torch.Tensor, q: torch.Tensor, metric: str, k1: int) -> float:
-    if metric == "ip":
-        truth = torch.topk(q @ x.T, 10, dim=1).indices
-    else:
-        d2 = (q * q).sum(1, keepdim=True) - 2 * q @ x.T + (x * x).sum(1)[None]
-        truth = torch.topk(-d2, 10, dim=1).indices
     got, _ = st.search(q, 10, k1, "auto")
-    hits = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(got.cpu(), truth.cpu()))
-    return hits / (10.0 * len(q))
+    return recall(got, raw_truth(x, q, metric, 10), 10)
+
+
+def _eps1(st: Store, x: torch.Tensor, ids: torch.Tensor, means: torch.Tensor) -> float:
+    return eps1_per_vector(st, x, ids, means)
 
 
 def run(n: int = 200_000, d: int = 96, nq: int = 500, metric: str = "l2", fractions=(0.01, 0.05, 0.1, 1.0),

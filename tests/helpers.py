@@ -10,6 +10,10 @@ TOL_FP32 = 1e-5    # relative, float32 scoring (scale: max(|s|, ||q|| ||x^||))
 TOL_FP16 = 2e-3    # relative, float16 tensor-core first level
 
 
+def _np(t):
+    return t.cpu().numpy() if torch.is_tensor(t) else np.asarray(t)
+
+
 def lib_store(x, means, bits1, bits2, metric, capacity=None):
     from paper_2402_02044_b300 import Store, build
     build.build()
@@ -39,8 +43,7 @@ def scale(q, xhat, metric):
 
 def check_scores(q, ids, scores, enc, means, metric, level, tol):
     """Every returned (id, score) pair matches the oracle's score of that id."""
-    ids = ids.cpu().numpy() if torch.is_tensor(ids) else ids
-    scores = scores.cpu().numpy() if torch.is_tensor(scores) else scores
+    ids, scores = _np(ids), _np(scores)
     for i in range(len(q)):
         sel = ids[i] >= 0
         if not sel.any():
@@ -60,71 +63,93 @@ def check_sorted(scores, metric):
     assert np.all(d >= 0) if metric == "l2" else np.all(d <= 0)
 
 
-def _tie_ok(score_of, boundary, q, xh_norm, metric, tol):
-    sc = max(abs(boundary), float(np.linalg.norm(q)) * xh_norm)
-    return abs(score_of - boundary) <= tol * sc * 2
+def _scale_of(q_i, xh_rows, s_ref):
+    """max(|s|, ||q|| ||x^||) per row: the tolerance scale of reading (xi)."""
+    qn = float(np.linalg.norm(np.asarray(q_i, dtype=np.float64)))
+    return np.maximum(np.abs(s_ref), qn * np.linalg.norm(xh_rows, axis=1))
 
 
-def check_topk_ids(q, gpu_ids, enc, means, metric, k, tol, live=None, level=1, cand_ids=None):
-    """The returned ids equal the oracle's top-k up to swaps among scores that
-    tie within the tolerance (single-stage search at ``level``)."""
-    gpu_ids = gpu_ids.cpu().numpy() if torch.is_tensor(gpu_ids) else gpu_ids
+def _check_boundary(i, pool, s_ref, scale_, got_ids, got_scores, metric, k, tol):
+    """One query's k best over ``pool``: the GPU's ids (best first) against the
+    oracle's, at the stated tolerance.
+
+    The GPU ranks by its own scores s', each within tol * scale of the
+    oracle's s (check_scores verifies that for every returned id).  So an id
+    the oracle ranks in and the GPU leaves out must have s within
+    tol * scale of the GPU's own k-th returned score s'_k (on the better
+    side), and an id the GPU returns but the oracle does not must have s
+    within tol * scale of s'_k on the worse side; every other id must agree.
+    """
+    order = O.best_first(s_ref, pool, metric)
+    n_exp = min(k, len(pool))
+    ref = pool[order[:n_exp]]
+    valid = got_ids >= 0
+    got = got_ids[valid]
+    assert len(got) == n_exp, (i, len(got), n_exp)
+    assert np.all(valid[:n_exp]), i
+    assert len(set(got.tolist())) == len(got), i
+    pos = {int(v): j for j, v in enumerate(pool)}
+    assert all(int(g) in pos for g in got), (i, "an id outside the searched set")
+    if n_exp == 0:
+        return
+    gk = float(got_scores[n_exp - 1])
+    sign = 1.0 if metric == O.L2 else -1.0
+    for h in set(ref.tolist()) - set(got.tolist()):
+        j = pos[h]
+        # left out by the GPU: s'(h) is no better than s'_k, and |s' - s| <= tol * scale
+        assert sign * (s_ref[j] - gk) >= -tol * scale_[j], (i, "missed", h, s_ref[j], gk)
+    for g in set(got.tolist()) - set(ref.tolist()):
+        j = pos[g]
+        assert sign * (s_ref[j] - gk) <= tol * scale_[j], (i, "extra", g, s_ref[j], gk)
+
+
+def _pool(i, n, live, cand_ids):
+    pool = np.nonzero(live)[0] if cand_ids is None else np.unique(
+        cand_ids[i][(cand_ids[i] >= 0) & (cand_ids[i] < n)])
+    return pool[live[pool]].astype(np.int64)
+
+
+def check_topk_ids(q, gpu_ids, gpu_scores, enc, means, metric, k, tol, live=None, level=1, cand_ids=None):
+    """A single-stage top-k (the k best live rows, or candidates, by the
+    score at ``level``): returned scores within ``tol`` of the oracle's and
+    ids equal to the oracle's up to ties at the k boundary within ``tol``
+    (``_check_boundary``)."""
+    gpu_ids = _np(gpu_ids)
+    gpu_scores = _np(gpu_scores)
+    check_scores(q, gpu_ids, gpu_scores, enc, means, metric, level, tol)
     n = len(enc["lower"])
     live = np.ones(n, bool) if live is None else live
     for i in range(len(q)):
-        pool = np.nonzero(live)[0] if cand_ids is None else np.unique(cand_ids[i][(cand_ids[i] >= 0) & (cand_ids[i] < n)])
-        pool = pool[live[pool]]
+        pool = _pool(i, n, live, cand_ids)
         xh = O.decode(O.take(enc, pool), means, level)
         s = O.score(q[i], xh, metric)[0]
-        order = O.best_first(s, pool, metric)
-        ref = pool[order[:k]]
-        got = gpu_ids[i][gpu_ids[i] >= 0]
-        assert len(got) == min(k, len(pool))
-        assert len(set(got.tolist())) == len(got)
-        if len(pool) == 0:
-            continue
-        kth = s[order[min(k, len(pool)) - 1]]
-        pos = {int(v): j for j, v in enumerate(pool)}
-        xn = np.linalg.norm(xh, axis=1)
-        for g in set(got.tolist()) ^ set(ref.tolist()):
-            j = pos[g]
-            assert _tie_ok(s[j], kth, q[i], xn[j], metric, tol), (i, g, s[j], kth)
+        _check_boundary(i, pool, s, _scale_of(q[i], xh, s), gpu_ids[i], gpu_scores[i], metric, k, tol)
 
 
-def check_two_level(q, gpu_ids, enc, means, metric, k1, k, tol, live=None, cand_ids=None):
-    """Two-stage search: the k1 best by first level, re-ranked by two levels.
-    Differences from the oracle must be explained by near-ties at the k1
-    boundary (first level) or at the k boundary (two levels)."""
-    gpu_ids = gpu_ids.cpu().numpy() if torch.is_tensor(gpu_ids) else gpu_ids
-    n = len(enc["lower"])
-    live = np.ones(n, bool) if live is None else live
+def check_two_level(q, gpu_ids, gpu_scores, first, enc, means, metric, k1, k, tol1, live=None, cand_ids=None):
+    """Two-stage search (first level k1 best, re-ranked by both levels to k).
+
+    ``first`` = (ids, scores) of the GPU's first stage alone for the same
+    queries (lvq_search_first_level, or the candidate search with k1 = 0 and
+    k = k1): the same scan gives the same k1 set.  Stage 1 is held to the
+    first-level tolerance ``tol1`` against the oracle's k1 best; stage 2 must
+    be the oracle's two-level re-rank of the GPU's own k1 set, at the float32
+    tolerance of the re-rank (both with ``_check_boundary``)."""
+    gpu_ids, gpu_scores = _np(gpu_ids), _np(gpu_scores)
+    fi, fs = _np(first[0]), _np(first[1])
+    check_topk_ids(q, fi, fs, enc, means, metric, k1, tol1, live=live, level=1, cand_ids=cand_ids)
+    check_scores(q, gpu_ids, gpu_scores, enc, means, metric, 2, TOL_FP32)
     for i in range(len(q)):
-        pool = np.nonzero(live)[0] if cand_ids is None else np.unique(cand_ids[i][(cand_ids[i] >= 0) & (cand_ids[i] < n)])
-        pool = pool[live[pool]]
-        x1 = O.decode(O.take(enc, pool), means, 1)
-        x2 = O.decode(O.take(enc, pool), means, 2)
-        s1 = O.score(q[i], x1, metric)[0]
-        s2 = O.score(q[i], x2, metric)[0]
-        o1 = O.best_first(s1, pool, metric)
-        c_idx = o1[:k1]
-        o2 = c_idx[O.best_first(s2[c_idx], pool[c_idx], metric)]
-        ref = pool[o2[:k]]
-        got = gpu_ids[i][gpu_ids[i] >= 0]
-        assert len(got) == min(k, len(pool)), (i, len(got))
-        kth1 = s1[o1[min(k1, len(pool)) - 1]]
-        kth2 = s2[o2[min(k, len(o2)) - 1]]
-        pos = {int(v): j for j, v in enumerate(pool)}
-        in_k1 = set(pool[c_idx].tolist())
-        n1 = np.linalg.norm(x1, axis=1)
-        n2 = np.linalg.norm(x2, axis=1)
-        for g in set(got.tolist()) ^ set(ref.tolist()):
-            j = pos[g]
-            tie2 = _tie_ok(s2[j], kth2, q[i], n2[j], metric, tol)
-            tie1 = _tie_ok(s1[j], kth1, q[i], n1[j], metric, tol)
-            # an id that the GPU returned but the oracle did not, or the
-            # reverse: a near-tie at the final boundary, or its first-level
-            # score sits at the k1 boundary (in or out of the candidate set)
-            assert tie2 or tie1 or (g not in in_k1 and tie1), (i, g)
+        pool = np.unique(fi[i][fi[i] >= 0]).astype(np.int64)
+        xh = O.decode(O.take(enc, pool), means, 2)
+        s = O.score(q[i], xh, metric)[0]
+        _check_boundary(i, pool, s, _scale_of(q[i], xh, s), gpu_ids[i], gpu_scores[i], metric, k, TOL_FP32)
+
+
+def check_rerank(q, gpu_ids, gpu_scores, enc, means, metric, cand, k, live=None):
+    """lvq_rerank: each query's live, distinct, in-range candidates ordered by
+    the two-level score, the k best, at the float32 tolerance."""
+    check_topk_ids(q, gpu_ids, gpu_scores, enc, means, metric, k, TOL_FP32, live=live, level=2, cand_ids=cand)
 
 
 def check_no_device_error(st):

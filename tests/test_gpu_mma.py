@@ -13,8 +13,8 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
-                     lib_store)
+from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids,
+                     check_two_level, gmm_case, lib_store)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,16 +54,16 @@ def test_tensor_core_first_level_and_search(case):
     fi, fs = st.first_level(qt, kk, "fp16")
     check_sorted(fs, metric)
     check_scores(q, fi, fs, enc, means, metric, 1, TOL_FP16)
-    check_topk_ids(q, fi, enc, means, metric, kk, TOL_FP16, level=1)
+    check_topk_ids(q, fi, fs, enc, means, metric, kk, TOL_FP16, level=1)
     gi, gs = st.search(qt, k, k1, "fp16")
     check_sorted(gs, metric)
     if b2 and k1:
         # re-rank distances are float32
         check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+        check_two_level(q, gi, gs, (fi, fs), enc, means, metric, k1, k, TOL_FP16)
     else:
         check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP16)
-        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP16, level=1)
+        check_topk_ids(q, gi, gs, enc, means, metric, k, TOL_FP16, level=1)
     check_no_device_error(st)
     st.close()
 
@@ -77,7 +77,7 @@ def test_every_tile_width_gives_the_same_candidates(mma_n):
     st.set_tuning(mma_n=mma_n)
     fi, fs = st.first_level(qt, 64, "fp16")
     check_scores(q, fi, fs, enc, means, "ip", 1, TOL_FP16)
-    check_topk_ids(q, fi, enc, means, "ip", 64, TOL_FP16, level=1)
+    check_topk_ids(q, fi, fs, enc, means, "ip", 64, TOL_FP16, level=1)
     # fewer CTAs than SMs: longer segments, same results
     st.set_tuning(mma_n=mma_n, mma_ctas=7)
     fi2, fs2 = st.first_level(qt, 64, "fp16")
@@ -98,7 +98,7 @@ def test_tensor_core_respects_deletes_and_padding():
     qt = torch.from_numpy(q).cuda()
     gi, gs = st.search(qt, 10, 40, "fp16")
     assert not np.isin(gi.cpu().numpy(), dead).any()
-    check_two_level(q, gi, enc, means, "l2", 40, 10, TOL_FP16, live=live)
+    check_two_level(q, gi, gs, st.first_level(qt, 40, "fp16"), enc, means, "l2", 40, 10, TOL_FP16, live=live)
     keep = np.nonzero(live)[0][:2]
     st.delete(torch.from_numpy(np.nonzero(live)[0][2:]).cuda())
     gi, gs = st.search(qt, 10, 40, "fp16")
@@ -108,13 +108,20 @@ def test_tensor_core_respects_deletes_and_padding():
     st.close()
 
 
-def test_fp16_and_fp32_paths_agree():
+def test_fp16_and_fp32_paths_both_match_the_oracle():
+    """The float16 tensor-core and the float32 first levels each give the
+    oracle's two-level search, element by element at their own tolerances,
+    and their recall@10 against the oracle's exact top-10 over the decoded
+    vectors is the oracle's own."""
     x, q, means = gmm_case(20000, 768, 64, "ip", 48, seed=12)
     st, ids = lib_store(x, means, 4, 8, "ip")
+    enc = O.encode(x, means, 4, 8)
     qt = torch.from_numpy(q).cuda()
-    a_i, a_s = st.search(qt, 10, 100, "fp16")
-    b_i, b_s = st.search(qt, 10, 100, "fp32")
-    agree = np.mean([len(set(r1) & set(r2)) / 10 for r1, r2 in zip(a_i.cpu().numpy(), b_i.cpu().numpy())])
-    assert agree >= 0.999
+    truth, _ = O.ground_truth(enc, means, q, 10, "ip")
+    ref_i, _ = O.search_exhaustive(enc, means, q, 100, 10, "ip")
+    for prec, tol in (("fp16", TOL_FP16), ("fp32", TOL_FP32)):
+        gi, gs = st.search(qt, 10, 100, prec)
+        check_two_level(q, gi, gs, st.first_level(qt, 100, prec), enc, means, "ip", 100, 10, tol)
+        assert abs(O.recall_at_k(gi.cpu().numpy(), truth, 10) - O.recall_at_k(ref_i, truth, 10)) <= 0.01, prec
     check_no_device_error(st)
     st.close()

@@ -13,8 +13,8 @@ import torch
 
 import oracle as O
 import synth
-from helpers import (TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
-                     lib_store)
+from helpers import (TOL_FP32, check_no_device_error, check_rerank, check_scores, check_sorted, check_topk_ids,
+                     check_two_level, gmm_case, lib_store)
 
 pytestmark = pytest.mark.gpu
 
@@ -110,16 +110,16 @@ def test_exhaustive_search_fp32(case):
     fi, fs = st.first_level(qt, kk, "fp32")
     check_sorted(fs, metric)
     check_scores(q, fi, fs, enc, means, metric, 1, TOL_FP32)
-    check_topk_ids(q, fi, enc, means, metric, kk, TOL_FP32, level=1)
+    check_topk_ids(q, fi, fs, enc, means, metric, kk, TOL_FP32, level=1)
     # the whole search
     gi, gs = st.search(qt, k, k1, "fp32")
     check_sorted(gs, metric)
     level = 2 if (b2 and k1) else 1
     check_scores(q, gi, gs, enc, means, metric, level, TOL_FP32)
     if level == 2:
-        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP32)
+        check_two_level(q, gi, gs, (fi, fs), enc, means, metric, k1, k, TOL_FP32)
     else:
-        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP32, level=1)
+        check_topk_ids(q, gi, gs, enc, means, metric, k, TOL_FP32, level=1)
     st.close()
 
 
@@ -138,7 +138,7 @@ def test_deletes_are_filtered_and_results_padded():
     qt = torch.from_numpy(q).cuda()
     gi, gs = st.search(qt, 10, 40, "fp32")
     assert not np.isin(gi.cpu().numpy(), dead).any()
-    check_two_level(q, gi, enc, means, "l2", 40, 10, TOL_FP32, live=live)
+    check_two_level(q, gi, gs, st.first_level(qt, 40, "fp32"), enc, means, "l2", 40, 10, TOL_FP32, live=live)
     # delete almost everything: fewer live rows than k -> padding
     keep = np.setdiff1d(np.arange(3000), dead)[[0, 7, -1]]
     rest = np.setdiff1d(np.arange(3000), np.r_[dead, keep])
@@ -185,25 +185,25 @@ def test_candidates_and_rerank(metric):
     gi, gs = st.search_candidates(qt, ct, 10, 50)
     check_sorted(gs, metric)
     check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-    check_two_level(q, gi, enc, means, metric, 50, 10, TOL_FP32, live=live, cand_ids=cand)
+    check_two_level(q, gi, gs, st.search_candidates(qt, ct, 50, 0), enc, means, metric, 50, 10, TOL_FP32,
+                    live=live, cand_ids=cand)
     # first level only (k1 = 0)
     fi, fs = st.search_candidates(qt, ct, 20, 0)
     check_scores(q, fi, fs, enc, means, metric, 1, TOL_FP32)
-    check_topk_ids(q, fi, enc, means, metric, 20, TOL_FP32, live=live, cand_ids=cand)
-    # a list holding every live id reproduces the exhaustive search
-    allc = np.tile(np.arange(n, dtype=np.int64), (4, 1))
+    check_topk_ids(q, fi, fs, enc, means, metric, 20, TOL_FP32, live=live, cand_ids=cand)
+    # a list holding every live id is the exhaustive search: both forms
+    # equal the oracle's exhaustive search, element by element
+    allc = torch.from_numpy(np.tile(np.arange(n, dtype=np.int64), (4, 1))).cuda()
     ei, es = st.search(qt[:4], 10, 50, "fp32")
-    ai, as_ = st.search_candidates(qt[:4], torch.from_numpy(allc).cuda(), 10, 50)
-    assert (ei == ai).float().mean() > 0.95
-    check_two_level(q[:4], ai, enc, means, metric, 50, 10, TOL_FP32, live=live)
-    # rerank of caller-given candidates
+    ai, as_ = st.search_candidates(qt[:4], allc, 10, 50)
+    check_two_level(q[:4], ei, es, st.first_level(qt[:4], 50, "fp32"), enc, means, metric, 50, 10, TOL_FP32,
+                    live=live)
+    check_two_level(q[:4], ai, as_, st.search_candidates(qt[:4], allc, 50, 0), enc, means, metric, 50, 10,
+                    TOL_FP32, live=live)
+    # rerank of caller-given candidates: the oracle's two-level order of
+    # each query's (live, distinct) candidates
     ri, rs = st.rerank(qt, ct[:, :200].contiguous(), 10)
-    ref_i, ref_s = O.rerank(enc, means, q, cand[:, :200], 10, metric, live)
-    check_scores(q, ri, rs, enc, means, metric, 2, TOL_FP32)
-    ri = ri.cpu().numpy()
-    for i in range(nq):
-        mism = set(ri[i].tolist()) ^ set(ref_i[i].tolist())
-        assert len(mism) <= 2
+    check_rerank(q, ri, rs, enc, means, metric, cand[:, :200], 10, live=live)
     st.close()
 
 
@@ -244,10 +244,11 @@ def test_candidates_widths_dims_means(case):
     check_sorted(gs, metric)
     if k1 and b2:
         check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP32, cand_ids=cand)
+        check_two_level(q, gi, gs, st.search_candidates(qt, ct, k1, 0), enc, means, metric, k1, k, TOL_FP32,
+                        cand_ids=cand)
     else:
         check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP32)
-        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP32, cand_ids=cand)
+        check_topk_ids(q, gi, gs, enc, means, metric, k, TOL_FP32, cand_ids=cand)
     check_no_device_error(st)
     st.close()
 
@@ -267,12 +268,14 @@ def test_candidates_many_queries_per_block_and_limits():
     cand = g.integers(0, n, (700, 90)).astype(np.int64)
     gi, gs = st.search_candidates(qt, torch.from_numpy(cand).cuda(), 10, 0)
     check_scores(q, gi, gs, enc, means, "ip", 1, TOL_FP32)
-    check_topk_ids(q, gi, enc, means, "ip", 10, TOL_FP32, cand_ids=cand)
+    check_topk_ids(q, gi, gs, enc, means, "ip", 10, TOL_FP32, cand_ids=cand)
     # the largest k1 (512) over 3000 candidates, re-ranked
     c2 = g.integers(0, n, (3, 3000)).astype(np.int64)
-    gi, gs = st.search_candidates(qt[:3], torch.from_numpy(c2).cuda(), 20, 512)
+    c2t = torch.from_numpy(c2).cuda()
+    gi, gs = st.search_candidates(qt[:3], c2t, 20, 512)
     check_scores(q[:3], gi, gs, enc, means, "ip", 2, TOL_FP32)
-    check_two_level(q[:3], gi, enc, means, "ip", 512, 20, TOL_FP32, cand_ids=c2)
+    check_two_level(q[:3], gi, gs, st.search_candidates(qt[:3], c2t, 512, 0), enc, means, "ip", 512, 20, TOL_FP32,
+                    cand_ids=c2)
     # one candidate; the longest list (every id, many times over)
     c3 = g.integers(0, n, (2, 1)).astype(np.int64)
     gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c3).cuda(), 5, 0)
@@ -280,7 +283,7 @@ def test_candidates_many_queries_per_block_and_limits():
     assert (gi[:, 0] == c3[:, 0]).all() and (gi[:, 1:] == -1).all()
     c4 = np.tile(np.arange(65536, dtype=np.int64) % n, (2, 1))
     gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c4).cuda(), 10, 0)
-    check_topk_ids(q[:2], gi, enc, means, "ip", 10, TOL_FP32)
+    check_topk_ids(q[:2], gi, gs, enc, means, "ip", 10, TOL_FP32)
     # all skipped / all deleted
     c5 = np.full((2, 40), -1, dtype=np.int64)
     gi, gs = st.search_candidates(qt[:2], torch.from_numpy(c5).cuda(), 5, 10)

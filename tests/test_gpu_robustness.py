@@ -22,3 +22,61 @@ def test_robustness_cases():
     # the stored two-level reconstructions are within a residual step of the
     # vectors, so the re-encode is almost as good as encoding them afresh
     assert upd["eps1_per_vector"] <= fresh["eps1_per_vector"] * 1.05
+
+
+def test_robustness_measures_equal_the_oracle():
+    """The experiment's first-level error (Eq. 5 per vector) and its exact
+    top-10 of the raw vectors are the oracle's on a small store, and its
+    recall is the oracle's recall of the same search results."""
+    import torch
+
+    import oracle as O
+    import synth
+    from paper_2402_02044_b300 import Store
+    from paper_2402_02044_b300 import robustness as R
+    for metric in ("l2", "ip"):
+        mix = synth.Mixture(d=48, n_comp=16, sigma=0.3, normalize=metric == "ip", seed=31)
+        x = mix.base(6000)
+        q = mix.queries(40)
+        mu = synth.sample_mean(x[:600])[None]
+        st = Store(48, 4, 8, mu, metric, len(x))
+        xt, qt = torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda()
+        st.insert(xt)
+        enc = O.encode(x, mu, 4, 8)
+        e = R.eps1_per_vector(st, xt, torch.arange(len(x), device="cuda"), torch.from_numpy(mu).cuda())
+        assert e == pytest.approx(O.eps_first(x, mu, enc) / len(x), rel=1e-5)
+        truth = R.raw_truth(xt, qt, metric, 10).cpu().numpy()
+        ref, _ = O.exact_knn(x, q, 10, metric)
+        assert np.array_equal(truth, ref)
+        got, _ = st.search(qt, 10, 100, "auto")
+        assert R.recall(got, torch.from_numpy(truth), 10) == pytest.approx(O.recall_at_k(got.cpu().numpy(), ref, 10))
+        st.close()
+
+
+@pytest.mark.parametrize("metric,n_means", [("l2", 4), ("ip", 1)])
+def test_decoded_truth_equals_the_oracle_ground_truth(metric, n_means):
+    """The float64 top-k over the store's decoded vectors (the recall ground
+    truth of the benchmark) is the oracle's exact k-NN over the decoded
+    vectors, deleted slots excluded, across several chunks."""
+    import torch
+
+    import oracle as O
+    from helpers import gmm_case, lib_store
+    from paper_2402_02044_b300 import robustness as R
+    x, q, means = gmm_case(7000, 40, 16, metric, 30, seed=57, n_means=n_means)
+    st, ids = lib_store(x, means, 4, 8, metric, capacity=7500)
+    dead = np.arange(3, 7000, 7)
+    st.delete(torch.from_numpy(dead).cuda())
+    live = np.ones(7000, bool)
+    live[dead] = False
+    mid = st.export(ids)["mean_id"].cpu().numpy()
+    enc = O.encode(x, means, 4, 8, mean_id=mid)
+    qt = torch.from_numpy(q).cuda()
+    for level in (1, 2):
+        got = R.decoded_truth(st, qt, 10, level=level, chunk=2048).cpu().numpy()
+        if level == 2:
+            ref, _ = O.ground_truth(enc, means, q, 10, metric, live=live)
+        else:
+            ref, _ = O.first_level_candidates(enc, means, q, 10, metric, live=live)
+        assert np.array_equal(got, ref), level
+    st.close()

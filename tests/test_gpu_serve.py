@@ -102,8 +102,12 @@ def test_updates_become_visible_at_epoch_boundaries():
         live_now[held] = False
         dele = g.choice(np.nonzero(live_now)[0], 500, replace=False)
         new = mix.rows(100 * step, 100 * step + 700, stream=12)
-        fd = srv.submit_delete(dele)
+        # the insert goes first: it is encoded when the scheduler stages it,
+        # before the boundary that frees the slots held at the previous one
+        # (a delete submitted first could reach a boundary of its own before
+        # the insert is staged, and that boundary would free them earlier)
         fi = srv.submit_insert(new)
+        fd = srv.submit_delete(dele)
         fq = srv.submit_query(new[:5], 10)          # queued behind the updates or before them
         ids_new = fi.result(timeout=60)
         assert fd.result(timeout=60) == 500
@@ -130,7 +134,10 @@ def test_updates_become_visible_at_epoch_boundaries():
         xs[i] = rows[int(i)]
     enc = O.encode(xs, means, 4, 8)
     from helpers import TOL_FP16, check_two_level
-    check_two_level(q, got_i, enc, means, "l2", 50, 10, TOL_FP16, live=live)
+    # the server runs the tensor-core first level (precision fp16); the same
+    # scan on the store gives its first stage
+    first = st.first_level(torch.from_numpy(q).cuda(), 50, "fp16")
+    check_two_level(q, got_i, got_s, first, enc, means, "l2", 50, 10, TOL_FP16, live=live)
     srv.close()
     st.close()
 

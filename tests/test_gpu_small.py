@@ -16,8 +16,8 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids, check_two_level, gmm_case,
-                     lib_store)
+from helpers import (TOL_FP16, TOL_FP32, check_no_device_error, check_scores, check_sorted, check_topk_ids,
+                     check_two_level, gmm_case, lib_store)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,15 +57,15 @@ def test_integer_first_level_and_search(case):
     fi, fs = st.first_level(qt, k1_, "int16")
     check_sorted(fs, metric)
     check_scores(q, fi[:, :kk], fs[:, :kk], enc, means, metric, 1, TOL_FP16)
-    check_topk_ids(q, fi[:, :kk], enc, means, metric, kk, TOL_FP16, level=1)
+    check_topk_ids(q, fi[:, :kk], fs[:, :kk], enc, means, metric, kk, TOL_FP16, level=1)
     gi, gs = st.search(qt, k, k1, "int16")
     check_sorted(gs, metric)
     if b2 and k1:
         check_scores(q, gi, gs, enc, means, metric, 2, TOL_FP32)
-        check_two_level(q, gi, enc, means, metric, k1, k, TOL_FP16)
+        check_two_level(q, gi, gs, (fi, fs), enc, means, metric, k1, k, TOL_FP16)
     else:
         check_scores(q, gi, gs, enc, means, metric, 1, TOL_FP16)
-        check_topk_ids(q, gi, enc, means, metric, k, TOL_FP16, level=1)
+        check_topk_ids(q, gi, gs, enc, means, metric, k, TOL_FP16, level=1)
     check_no_device_error(st)
     st.close()
 
@@ -89,11 +89,12 @@ def test_auto_takes_the_integer_scan_for_small_batches():
     L.lvq_profile_enable(st.handle, False)
     with pytest.raises(L.LVQError):
         st.first_level(qt[:5], 100, "int16")
-    # the integer and float32 first levels choose the same candidates
-    f_i, _ = st.search(qt[:4], 10, 100, "fp32")
-    g_i, _ = st.search(qt[:4], 10, 100, "int16")
-    agree = np.mean([len(set(r1) & set(r2)) / 10 for r1, r2 in zip(f_i.cpu().numpy(), g_i.cpu().numpy())])
-    assert agree >= 0.999
+    # the integer and float32 first levels each give the oracle's two-level
+    # search, element by element at their own tolerances
+    enc = O.encode(x, means, 4, 8)
+    for prec, tol in (("fp32", TOL_FP32), ("int16", TOL_FP16)):
+        gi, gs = st.search(qt[:4], 10, 100, prec)
+        check_two_level(q[:4], gi, gs, st.first_level(qt[:4], 100, prec), enc, means, "ip", 100, 10, tol)
     check_no_device_error(st)
     st.close()
 
@@ -111,7 +112,7 @@ def test_integer_scan_respects_deletes_and_zero_queries():
     qt = torch.from_numpy(q).cuda()
     gi, gs = st.search(qt, 10, 40, "int16")
     assert not np.isin(gi.cpu().numpy(), dead).any()
-    check_two_level(q, gi, enc, means, "l2", 40, 10, TOL_FP16, live=live)
+    check_two_level(q, gi, gs, st.first_level(qt, 40, "int16"), enc, means, "l2", 40, 10, TOL_FP16, live=live)
     keep = np.nonzero(live)[0][:2]
     st.delete(torch.from_numpy(np.nonzero(live)[0][2:]).cuda())
     gi, gs = st.search(qt, 10, 40, "int16")

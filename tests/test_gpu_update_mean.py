@@ -60,10 +60,10 @@ def test_update_mean_matches_the_oracle(metric, bits1, bits2):
     k1 = 50 if bits2 else 0
     gi, gs = st.search(qt, 10, k1, "fp32")
     if bits2:
-        check_two_level(q, gi, ref, means2, metric, k1, 10, TOL_FP32, live=live)
+        check_two_level(q, gi, gs, st.first_level(qt, k1, "fp32"), ref, means2, metric, k1, 10, TOL_FP32, live=live)
     else:
         from helpers import check_topk_ids
-        check_topk_ids(q, gi, ref, means2, metric, 10, TOL_FP32, live=live, level=1)
+        check_topk_ids(q, gi, gs, ref, means2, metric, 10, TOL_FP32, live=live, level=1)
     check_no_device_error(st)
     st.close()
 

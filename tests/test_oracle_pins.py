@@ -41,6 +41,18 @@ def test_hand_worked_encodings(case):
         np.testing.assert_allclose(x2 - x[0].astype(np.float64), case["decoded2_minus_x"], rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("case", [c for c in _cases() if "eps1" in c], ids=lambda c: c["name"])
+def test_hand_worked_quantisation_errors(case):
+    # Eq. 5 (eps1) and its two-level analogue (eps2), worked by hand: values,
+    # not relations, so a squared difference replaced by an absolute one, a
+    # centre dropped on both sides or a missing residual term all fail here.
+    x = np.array([case["x"]], dtype=F32)
+    means = np.array(case["means"], dtype=F32)
+    enc = O.encode(x, means, case["bits1"], case["bits2"])
+    assert O.eps_first(x, means, enc) == pytest.approx(case["eps1"], rel=1e-12, abs=1e-300)
+    assert O.eps_second(x, means, enc) == pytest.approx(case["eps2"], rel=1e-12, abs=1e-300)
+
+
 # ------------------------------------------------------------------ invariants
 
 def _gmm(n=3000, d=96, comps=16, normalize=False, seed=7):
@@ -257,6 +269,20 @@ def test_rerank_uses_two_levels_and_gather_equals_exhaustive():
         assert gt[i].tolist() == _brute_topk(s2[i], np.arange(500), 10, O.L2)
 
 
+@pytest.mark.parametrize("metric", [O.L2, O.IP])
+def test_exact_knn_of_raw_vectors_by_brute_force(metric):
+    # Sec. 2.1: the k nearest by the raw vectors, ties to the lower id
+    g = np.random.default_rng(23)
+    x = g.integers(-3, 4, size=(40, 6)).astype(F32)
+    q = g.integers(-3, 4, size=(3, 6)).astype(F32)
+    ids, s = O.exact_knn(x, q, 7, metric, chunk=16)
+    for i in range(len(q)):
+        sc = np.array([sum(float(q[i, j]) * float(x[r, j]) for j in range(6)) if metric == O.IP
+                       else sum((float(q[i, j]) - float(x[r, j])) ** 2 for j in range(6)) for r in range(40)])
+        assert ids[i].tolist() == _brute_topk(sc, np.arange(40), 7, metric)
+        assert s[i].tolist() == [sc[r] for r in ids[i]]
+
+
 def test_recall_at_k():
     assert O.recall_at_k(np.array([[1, 2, 3, 4]]), np.array([[4, 3, 9, 8]]), 4) == 0.5
     assert O.recall_at_k(np.array([[1, -1]]), np.array([[1, 2]]), 2) == 0.5
@@ -299,6 +325,18 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(O.lvq, "quantize", div_form)
     assert O.encode(np.array([c1["x"]], F32), np.array(c1["means"], F32), 2)["codes1"][0].tolist() != c1["codes1"]
     monkeypatch.undo()
+
+    # eps with absolute instead of squared differences, or with the centre
+    # dropped from both the vector and its reconstruction, misses the
+    # hand-worked value of Eq. 5
+    ce = [c for c in _cases() if c["name"].startswith("non-zero first-level")][0]
+    xe, me = np.array([ce["x"]], F32), np.array(ce["means"], F32)
+    enc_e = O.encode(xe, me, ce["bits1"], ce["bits2"])
+    x1 = O.decode_first(enc_e, me)
+    abs_sum = float(np.abs(xe.astype(np.float64) - x1).sum())
+    no_centre = float(((xe.astype(np.float64) - (x1 - me.astype(np.float64))) ** 2).sum())
+    assert abs_sum != pytest.approx(ce["eps1"]) and no_centre != pytest.approx(ce["eps1"])
+    assert O.eps_first(xe, me, enc_e) == pytest.approx(ce["eps1"])
 
     # a decode that forgets the centre breaks the inner-product factorisation
     mix = synth.Mixture(d=16, n_comp=4, sigma=0.3, seed=3)
