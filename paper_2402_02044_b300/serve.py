@@ -68,6 +68,9 @@ class Request:
     epoch: int = -1
     group: Optional["_Group"] = None  # the request this one is a part of
     part: int = 0
+    t_launch: float = 0.0  # host time its (first) batch was launched
+    lane: int = -1
+    pinned: Optional[torch.Tensor] = None  # update rows / ids in page-locked memory (pinned by the client)
 
 
 class _Group:
@@ -80,6 +83,7 @@ class _Group:
         self.future = future
         self.rows = rows
         self.epoch = -1
+        self.t_launch = 0.0
 
 
 def request_bytes(kind: str, n: int, d: int, k: int) -> int:
@@ -147,12 +151,25 @@ class LatencyStats:
         self.rows = 0
         self.t0 = None
         self.t1 = None
+        self.trace = []  # (t_submit, t_launch, t_done, rows, lane, epoch) per request
 
-    def add(self, t_submit: float, t_done: float, rows: int):
+    def add(self, t_submit: float, t_done: float, rows: int, t_launch: float = 0.0, lane: int = -1,
+            epoch: int = -1):
         self.lat.append(t_done - t_submit)
         self.rows += rows
         self.t0 = t_submit if self.t0 is None else min(self.t0, t_submit)
         self.t1 = t_done if self.t1 is None else max(self.t1, t_done)
+        self.trace.append((t_submit, t_launch, t_done, rows, lane, epoch))
+
+    def slowest(self, n: int = 5) -> list:
+        """The n slowest requests: latency split into the wait before their
+        (first) batch was launched and the time from launch to completion."""
+        out = []
+        for ts, tl, td, rows, lane, ep in sorted(self.trace, key=lambda r: r[0] - r[2])[:n]:
+            out.append({"ms": (td - ts) * 1e3, "wait_ms": (tl - ts) * 1e3 if tl else None,
+                        "run_ms": (td - tl) * 1e3 if tl else None, "rows": rows, "lane": lane,
+                        "at_s": ts - self.t0, "epoch": ep})
+        return out
 
     def summary(self) -> dict:
         if not self.lat:
@@ -182,7 +199,7 @@ class _Lane:
 class Server:
     def __init__(self, store: Store, lanes: int = 2, max_batch: int = 4096, k1: int = 100, kmax: int = 100,
                  precision: str = "auto", hbm_budget: Optional[int] = None, use_graphs: bool = False,
-                 tuning: Optional[dict] = None, warmup: bool = True, update_rows: int = 16384):
+                 tuning: Optional[dict] = None, warmup: bool = True):
         self.store = store
         self.d = store.d
         self.k1 = k1 if store.bits2 else 0
@@ -197,8 +214,6 @@ class Server:
         self.admission = Admission(hbm_budget)
         self.lanes = [_Lane(store, self.d, max_batch, kmax, max(self.k1, kmax)) for _ in range(lanes)]
         self.upd_stream = torch.cuda.Stream()
-        self.upd_pin = torch.empty((max(1, update_rows), self.d), dtype=torch.float32).pin_memory()
-        self.upd_pin_ev = None
         # the visibility bitmaps of the current and the previous epoch
         self.snaps = [store.live_snapshot(stream=self.upd_stream)]
         self.snaps.append(torch.empty_like(self.snaps[0]))
@@ -266,11 +281,15 @@ class Server:
 
     def submit_insert(self, x: np.ndarray) -> Future:
         x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, self.d)
-        return self._submit(Request(INSERT, x, nbytes=request_bytes(INSERT, len(x), self.d, 0)))
+        # page-locked on the caller's thread, so that the scheduler's copy to
+        # the device neither blocks it nor allocates pinned memory there
+        return self._submit(Request(INSERT, x, nbytes=request_bytes(INSERT, len(x), self.d, 0),
+                                    pinned=torch.from_numpy(x).pin_memory()))
 
     def submit_delete(self, ids: np.ndarray) -> Future:
         ids = np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
-        return self._submit(Request(DELETE, ids, nbytes=request_bytes(DELETE, len(ids), self.d, 0)))
+        return self._submit(Request(DELETE, ids, nbytes=request_bytes(DELETE, len(ids), self.d, 0),
+                                    pinned=torch.from_numpy(ids).pin_memory()))
 
     def reset_stats(self):
         """Forget the latencies recorded so far (e.g. after a warm-up)."""
@@ -281,7 +300,8 @@ class Server:
     def stats_summary(self) -> dict:
         with self._lock:
             s = self.stats.summary()
-            s.update(rejected=self.rejected, epochs=self.epoch - self.epoch_base, hbm_budget=self.admission.budget)
+            s.update(rejected=self.rejected, epochs=self.epoch - self.epoch_base, hbm_budget=self.admission.budget,
+                     slowest=self.stats.slowest())
             return s
 
     def drain(self, timeout: float = 60.0):
@@ -371,14 +391,14 @@ class Server:
                     g = r.group
                     if g is None:
                         r.future.set_result(res + (r.epoch,))
-                        self.stats.add(r.t_submit, t, n)
+                        self.stats.add(r.t_submit, t, n, r.t_launch, r.lane, r.epoch)
                         continue
                     g.results[r.part] = res
                     g.remaining -= 1
                     if g.remaining == 0:
                         g.future.set_result((np.concatenate([a for a, _ in g.results]),
                                              np.concatenate([b for _, b in g.results]), g.epoch))
-                        self.stats.add(r.t_submit, t, g.rows)
+                        self.stats.add(r.t_submit, t, g.rows, g.t_launch, r.lane, g.epoch)
             done_any = True
         keep = []
         for item in self.inflight_upd:
@@ -404,23 +424,15 @@ class Server:
             return False
         with torch.cuda.stream(self.upd_stream):
             for r in reqs:
+                # the rows (ids) reach the device in stream order, without a
+                # host wait: the copy is from memory the client pinned
+                dev = torch.empty(r.data.shape, dtype=r.pinned.dtype, device="cuda")
+                dev.copy_(r.pinned, non_blocking=True)
                 if r.kind == INSERT:
-                    x = torch.empty(r.data.shape, dtype=torch.float32, device="cuda")
-                    # through a pinned staging buffer allocated once (pinning
-                    # each request's rows would allocate page-locked memory on
-                    # the scheduler's path)
-                    for a in range(0, len(r.data), len(self.upd_pin)):
-                        b = min(len(r.data), a + len(self.upd_pin))
-                        if self.upd_pin_ev is not None:
-                            self.upd_pin_ev.synchronize()
-                        self.upd_pin[:b - a].copy_(torch.from_numpy(r.data[a:b]))
-                        x[a:b].copy_(self.upd_pin[:b - a], non_blocking=True)
-                        self.upd_pin_ev = torch.cuda.Event()
-                        self.upd_pin_ev.record(self.upd_stream)
-                    ids = self.store.insert_deferred(x, stream=self.upd_stream)
-                    self.staged.append((ids, x, r))
+                    ids = self.store.insert_deferred(dev, stream=self.upd_stream)
+                    self.staged.append((ids, dev, r))
                 else:
-                    self.deletes.append(r)
+                    self.deletes.append((r, dev))
         return True
 
     def _epoch_boundary(self):
@@ -444,8 +456,7 @@ class Server:
                 ev = torch.cuda.Event()
                 ev.record(s)
                 self.inflight_upd.append((ev, r, ids_host, INSERT))
-            for r in self.deletes:
-                ids = torch.from_numpy(r.data).cuda(non_blocking=True)
+            for r, ids in self.deletes:
                 out = self.store.delete_hold(ids, stream=s)
                 self.held.append((e + 1, ids))
                 ev = torch.cuda.Event()
@@ -495,10 +506,16 @@ class Server:
                 break
             rows = sum(r.data.shape[0] for r in batch)
             kb = max(r.k for r in batch)
+            t_l = time.perf_counter()
+            lane_idx = self.lanes.index(lane)
             for r in batch:
                 r.epoch = epoch
+                r.t_launch = t_l
+                r.lane = lane_idx
                 if r.group is not None:
                     r.group.epoch = epoch
+                    if not r.group.t_launch:
+                        r.group.t_launch = t_l
             self._run_batch(lane, batch, rows, kb, epoch)
             launched = True
         return launched
