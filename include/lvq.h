@@ -69,13 +69,24 @@ typedef enum { LVQ_L2 = 0, LVQ_IP = 1 } lvq_metric;
  *                 to 4 queries, the tensor cores above that. */
 typedef enum { LVQ_FP32 = 0, LVQ_FP16_MMA = 1, LVQ_AUTO = 2, LVQ_INT16 = 3 } lvq_precision;
 
+/* lvq_config.flags */
+enum {
+  /* The residual level on the App. C listing's signed grid (step D / 2^B2,
+   * codes round(r / step) half to even, clipped to [-2^(B2-1), 2^(B2-1)-1],
+   * stored as int8) instead of the text's Q_{B2,-D/2,D/2} (Sec. 2.2). */
+  LVQ_FLAG_LISTING_RESIDUAL = 1
+};
+
 typedef struct {
   int32_t d;        /* dimensionality, 1 .. 4096 */
-  int32_t bits1;    /* first-level bits B1: 4 or 8 */
-  int32_t bits2;    /* residual bits B2: 0 (LVQ-B1) or 8 (LVQ-B1x8) */
+  int32_t bits1;    /* first-level bits B1: 2 .. 8 (Sec. 3.3 explores B1 and
+                       B2); B1 <= 4 is stored in 4-bit containers, B1 >= 5
+                       in bytes, and every scan reads those containers */
+  int32_t bits2;    /* residual bits B2: 0 (LVQ-B1) or 2 .. 8 (LVQ-B1xB2),
+                       stored in bytes */
   int32_t n_means;  /* M centring means, 1 .. 256 (M = 1 is plain LVQ) */
   int32_t metric;   /* lvq_metric */
-  int32_t reserved; /* must be 0 */
+  int32_t flags;    /* LVQ_FLAG_* ; other bits must be 0 */
   int64_t capacity; /* number of slots, 1 .. 2^31 - 1 */
 } lvq_config;
 
@@ -117,14 +128,16 @@ lvq_status lvq_store_view(const lvq_store *base, lvq_store **out);
 /* Encode n vectors without touching the store (Eq. 1-3, Def. 1, Sec. 2.2).
  * x: n x d float32, row-major.
  * codes1: n x d uint8, one first-level code per byte, in [0, 2^B1 - 1].
- * codes2: n x d uint8 residual codes in [0, 255], or NULL (required when
- *   bits2 = 8, ignored when bits2 = 0).
+ * codes2: n x d uint8 residual codes in [0, 2^B2 - 1] (the listing's signed
+ *   grid: int8 bytes in [-2^(B2-1), 2^(B2-1) - 1]), or NULL (required when
+ *   bits2 > 0, ignored when bits2 = 0).
  * lower, step: n float32 each, l(x) and D of the vector.
  * mean_id: n uint8, index of the centring mean.
  * Every float32 step is rounded separately (no fused multiply-add):
  *   y = x - mu*, l = min y, D = (max y - l)/(2^B1 - 1),
  *   c = clamp(floor(fl(1/D') * (y - l) + 1/2)), D' = D or 1 when D = 0,
- *   r = y - (D c + l), c2 likewise with l2 = -D/2, D2 = D/(2^B2 - 1). */
+ *   r = y - (D c + l), c2 likewise with l2 = -D/2, D2 = D/(2^B2 - 1) (or on
+ *   the listing's signed grid, LVQ_FLAG_LISTING_RESIDUAL). */
 lvq_status lvq_encode(const lvq_store *store, const float *x, int64_t n, uint8_t *codes1,
                       uint8_t *codes2, float *lower, float *step, uint8_t *mean_id,
                       lvq_stream_t stream);
@@ -269,7 +282,7 @@ lvq_status lvq_search_candidates(const lvq_store *store, const float *q, int64_t
 
 /* Re-rank given candidates with both levels (Sec. 2.2, App. C), float32.
  * ids: nq x k1 int64 (-1, out-of-range, deleted and repeated ids skipped).
- * k <= k1 <= 4096.  Outputs nq x k.  Needs a store with bits2 = 8. */
+ * k <= k1 <= 4096.  Outputs nq x k.  Needs a store with a residual level. */
 lvq_status lvq_rerank(const lvq_store *store, const float *q, int64_t nq, const int64_t *ids,
                       int32_t k1, int32_t k, int64_t *out_ids, float *out_scores,
                       lvq_stream_t stream);

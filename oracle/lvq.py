@@ -13,7 +13,10 @@ reason in the design notes of the repository):
         a division.
 * (ii)  rounding is floor(t + 1/2) (Eq. 2) at both levels.
 * (iii) the second level uses the text's grid Q_{B2,-Delta/2,Delta/2}
-        (Sec. 2.2, Def. 1): unsigned codes, step Delta/(2^B2 - 1).
+        (Sec. 2.2, Def. 1): unsigned codes, step Delta/(2^B2 - 1).  The App. C
+        listing's signed grid (step Delta/2^B2, codes rounded half to even and
+        clipped to [-2^(B2-1), 2^(B2-1) - 1], no offset) is the option
+        grid2="listing".
 * (iv)  a constant centred vector (Delta = 0) is coded with a unit step
         (all codes 0, as in App. C) but Delta = 0 is stored, so it decodes
         exactly.
@@ -39,7 +42,7 @@ __all__ = [
     "L2", "IP", "assign_means", "quantize", "residual_grid", "encode", "decode_first",
     "decode_second", "decode", "score", "best_first", "topk", "search_exhaustive",
     "search_candidates", "rerank", "ground_truth", "recall_at_k", "eps_first", "eps_second",
-    "SlotReplay", "StoreFull", "pad_value", "take", "first_level_candidates",
+    "SlotReplay", "StoreFull", "pad_value", "take", "first_level_candidates", "quantize_signed",
     "reconstruct_f32", "update_mean", "beam_search", "exact_knn",
 ]
 
@@ -84,28 +87,47 @@ def quantize(v: np.ndarray, lower: np.ndarray, step: np.ndarray, bits: int) -> n
     return np.clip(codes, 0, (1 << bits) - 1).astype(np.uint8)
 
 
-def residual_grid(step: np.ndarray, bits2: int):
-    """Lower bound and step of the second-level quantiser Q_{B2,-D/2,D/2}
-    (Sec. 2.2, Def. 1): l2 = -step/2 (exact) and step2 = step/(2^B2 - 1),
-    rounded to float32."""
+def residual_grid(step: np.ndarray, bits2: int, grid2: str = "text"):
+    """Lower bound and step of the second-level quantiser.
+
+    "text": Q_{B2,-D/2,D/2} (Sec. 2.2, Def. 1): l2 = -step/2 (exact) and
+    step2 = step/(2^B2 - 1), rounded to float32.
+    "listing": the signed grid of App. C: l2 = 0, step2 = step/2^B2 (a power
+    of two: exact)."""
     step = np.asarray(step, dtype=F32)
+    if grid2 == "listing":
+        return np.zeros_like(step), (step / F32(1 << bits2)).astype(F32)
     lower2 = (-step * F32(0.5)).astype(F32)
     step2 = (step / F32((1 << bits2) - 1)).astype(F32)
     return lower2, step2
 
 
-def encode(x: np.ndarray, means: np.ndarray, bits1: int, bits2: int = 0, mean_id=None) -> dict:
+def quantize_signed(v: np.ndarray, step: np.ndarray, bits: int) -> np.ndarray:
+    """The App. C listing's residual codes: round(v * (1/step)) half to even,
+    clipped to [-2^(B-1), 2^(B-1) - 1], in float32 (a zero step is replaced
+    by 1 for the codes)."""
+    v = np.asarray(v, dtype=F32)
+    step = np.asarray(step, dtype=F32)
+    step_c = np.where(step == F32(0), F32(1), step).astype(F32)
+    inv = (F32(1) / step_c).astype(F32)
+    t = (inv[:, None] * v).astype(F32)
+    half = 1 << (bits - 1)
+    return np.clip(np.round(t), -half, half - 1).astype(np.int8)
+
+
+def encode(x: np.ndarray, means: np.ndarray, bits1: int, bits2: int = 0, mean_id=None, grid2: str = "text") -> dict:
     """LVQ-B1 or LVQ-B1xB2 of each row of ``x`` (M-LVQ when several means).
 
     Steps: nearest centre (Def. 1) -> centred y = x - mu* (float32) ->
     bounds u = max y, l = min y (Eq. 1) -> step D = (u - l)/(2^B1 - 1)
     (Eq. 2) -> first-level codes (Eq. 2, 3) -> centred reconstruction
     y^ = D*c + l -> residual r = y - y^ (Sec. 2.2) -> second-level codes of r
-    on the grid of ``residual_grid``.
+    on the grid of ``residual_grid`` (``grid2``: "text" or "listing").
 
     Returns a dict with ``codes1`` [n, d] uint8 (one code per byte),
-    ``codes2`` [n, d] uint8 or None, ``lower`` and ``step`` float32 [n],
-    ``mean_id`` uint8 [n] and the bit widths."""
+    ``codes2`` [n, d] (uint8 on the text grid, int8 on the listing's) or
+    None, ``lower`` and ``step`` float32 [n], ``mean_id`` uint8 [n], the bit
+    widths and the residual grid."""
     x = np.asarray(x, dtype=F32)
     means = np.asarray(means, dtype=F32).reshape(-1, x.shape[1])
     m = assign_means(x, means) if mean_id is None else np.asarray(mean_id, dtype=np.uint8)
@@ -116,11 +138,11 @@ def encode(x: np.ndarray, means: np.ndarray, bits1: int, bits2: int = 0, mean_id
     codes1 = quantize(y, lower, step, bits1)
     y_hat = ((step[:, None] * codes1.astype(F32)).astype(F32) + lower[:, None]).astype(F32)
     out = dict(codes1=codes1, codes2=None, lower=lower, step=step, mean_id=m,
-               bits1=bits1, bits2=bits2)
+               bits1=bits1, bits2=bits2, grid2=grid2)
     if bits2:
         r = (y - y_hat).astype(F32)
-        lower2, step2 = residual_grid(step, bits2)
-        out["codes2"] = quantize(r, lower2, step2, bits2)
+        lower2, step2 = residual_grid(step, bits2, grid2)
+        out["codes2"] = quantize_signed(r, step2, bits2) if grid2 == "listing" else quantize(r, lower2, step2, bits2)
     return out
 
 
@@ -150,7 +172,7 @@ def decode_second(enc: dict, means: np.ndarray) -> np.ndarray:
     x1 = decode_first(enc, means)
     if not enc.get("bits2"):
         return x1
-    lower2, step2 = residual_grid(enc["step"], enc["bits2"])
+    lower2, step2 = residual_grid(enc["step"], enc["bits2"], enc.get("grid2", "text"))
     return x1 + lower2.astype(F64)[:, None] + step2.astype(F64)[:, None] * enc["codes2"].astype(F64)
 
 
@@ -383,7 +405,7 @@ def reconstruct_f32(enc: dict, means) -> np.ndarray:
     step = enc["step"].astype(F32)[:, None]
     y = ((step * enc["codes1"].astype(F32)).astype(F32) + enc["lower"].astype(F32)[:, None]).astype(F32)
     if enc.get("bits2"):
-        lower2, step2 = residual_grid(enc["step"], enc["bits2"])
+        lower2, step2 = residual_grid(enc["step"], enc["bits2"], enc.get("grid2", "text"))
         r = ((step2[:, None] * enc["codes2"].astype(F32)).astype(F32) + lower2[:, None]).astype(F32)
         y = (y + r).astype(F32)
     return (means[enc["mean_id"].astype(np.int64)] + y).astype(F32)
@@ -400,7 +422,8 @@ def update_mean(enc: dict, means, m: int, new_mean, live=None):
     means2 = np.array(np.asarray(means, dtype=F32).reshape(-1, d), copy=True)
     x = reconstruct_f32(take(enc, rows), means2)
     means2[m] = np.asarray(new_mean, dtype=F32)
-    e = encode(x, means2, enc["bits1"], enc.get("bits2") or 0, mean_id=np.full(len(rows), m, dtype=np.uint8))
+    e = encode(x, means2, enc["bits1"], enc.get("bits2") or 0, mean_id=np.full(len(rows), m, dtype=np.uint8),
+               grid2=enc.get("grid2", "text"))
     out = dict(enc)
     for key in ("codes1", "codes2", "lower", "step"):
         if enc.get(key) is not None:

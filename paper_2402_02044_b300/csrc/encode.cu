@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
   const int warps = blockDim.x >> 5;
   const int d = st.d;
   const int groups = (d + 7) >> 3;
-  const float maxc1 = (float)((1 << st.bits1) - 1);
+  const float maxc1 = (float)st.lev1;  // 2^B1 - 1
   if (out.abort_flag && *out.abort_flag) return;
 
   for (int64_t v = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); v < n;
@@ -104,12 +104,19 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
     // Eq. 2: step and its reciprocal (a zero step codes with a unit step).
     const float step = __fdiv_rn(__fsub_rn(hi, lo), maxc1);
     const float inv = __frcp_rn(step == 0.0f ? 1.0f : step);
+    // Second level: the text's grid Q_{B2,-D/2,D/2} (Sec. 2.2) or the App. C
+    // listing's signed grid (step D/2^B2, exact; no offset)
     float step2 = 0.0f, inv2 = 0.0f, lo2 = 0.0f;
     if (st.bits2) {
-      lo2 = __fmul_rn(-step, 0.5f);
-      step2 = __fdiv_rn(step, 255.0f);
+      if (st.grid2) {
+        step2 = __fmul_rn(step, __int_as_float((127 - st.b2) << 23));
+      } else {
+        lo2 = __fmul_rn(-step, 0.5f);
+        step2 = __fdiv_rn(step, (float)st.lev2);
+      }
       inv2 = __frcp_rn(step2 == 0.0f ? 1.0f : step2);
     }
+    const float half2 = (float)(1 << (st.b2 > 0 ? st.b2 - 1 : 0));
     uint32_t c1[WPL][8], c2[WPL][8];
     float nrm = 0.0f;
 #pragma unroll
@@ -128,7 +135,14 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
           nrm = __fmaf_rn(xh, xh, nrm);
           if (st.bits2) {
             const float r = __fsub_rn(y, yhat);
-            c2[i][e] = quant_code(r, lo2, inv2, 255.0f);
+            if (st.grid2) {
+              // round half to even, clipped to [-2^(B2-1), 2^(B2-1) - 1],
+              // kept as the two's complement byte
+              const float t = fminf(fmaxf(rintf(__fmul_rn(inv2, r)), -half2), half2 - 1.0f);
+              c2[i][e] = (uint32_t)((int)t & 255);
+            } else {
+              c2[i][e] = quant_code(r, lo2, inv2, (float)st.lev2);
+            }
           }
         }
       }
@@ -442,7 +456,8 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(DeviceStore st, const 
   if (i >= n) return;
   const int64_t s = list[i];
   const float lo = st.lower[s], step = st.step[s];
-  const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+  const float lo2 = st.grid2 ? 0.0f : __fmul_rn(-step, 0.5f);
+  const float step2 = st.grid2 ? __fmul_rn(step, __int_as_float((127 - st.b2) << 23)) : __fdiv_rn(step, (float)st.lev2);
   const uint8_t* r1 = st.codes1 + s * st.row1;
   const uint8_t* r2 = st.bits2 ? st.codes2 + s * st.row2 : nullptr;
   for (int j = lane; j < st.d; j += 32) {
@@ -456,7 +471,10 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(DeviceStore st, const 
       c = r1[j];
     }
     float y = __fadd_rn(__fmul_rn(step, (float)c), lo);
-    if (r2) y = __fadd_rn(y, __fadd_rn(__fmul_rn(step2, (float)r2[j]), lo2));
+    if (r2) {
+      const float c2 = st.grid2 ? (float)(int8_t)r2[j] : (float)r2[j];
+      y = __fadd_rn(y, __fadd_rn(__fmul_rn(step2, c2), lo2));
+    }
     x[i * st.d + j] = __fadd_rn(mu[j], y);
   }
 }

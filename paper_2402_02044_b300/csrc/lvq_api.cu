@@ -303,11 +303,11 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   if (!cfg || !means_host || !out) return LVQ_EINVAL;
   *out = nullptr;
   if (cfg->d < 1 || cfg->d > kMaxD) return LVQ_EINVAL;
-  if (cfg->bits1 != 4 && cfg->bits1 != 8) return LVQ_EINVAL;
-  if (cfg->bits2 != 0 && cfg->bits2 != 8) return LVQ_EINVAL;
+  if (cfg->bits1 < 2 || cfg->bits1 > 8) return LVQ_EINVAL;
+  if (cfg->bits2 != 0 && (cfg->bits2 < 2 || cfg->bits2 > 8)) return LVQ_EINVAL;
   if (cfg->n_means < 1 || cfg->n_means > kMaxMeans) return LVQ_EINVAL;
   if (cfg->metric != LVQ_L2 && cfg->metric != LVQ_IP) return LVQ_EINVAL;
-  if (cfg->reserved != 0) return LVQ_EINVAL;
+  if ((cfg->flags & ~LVQ_FLAG_LISTING_RESIDUAL) != 0) return LVQ_EINVAL;
   if (cfg->capacity < 1 || cfg->capacity > (int64_t)INT32_MAX) return LVQ_EINVAL;
   lvq_store* s = new (std::nothrow) lvq_store();
   if (!s) return LVQ_ENOMEM;
@@ -316,12 +316,18 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   DeviceStore& st = s->ds;
   memset(&st, 0, sizeof(st));
   st.d = cfg->d;
-  st.bits1 = cfg->bits1;
-  st.bits2 = cfg->bits2;
+  // codes live in 4-bit (B1 <= 4) or 8-bit containers; residuals in bytes
+  st.bits1 = cfg->bits1 <= 4 ? 4 : 8;
+  st.bits2 = cfg->bits2 ? 8 : 0;
+  st.b1 = cfg->bits1;
+  st.b2 = cfg->bits2;
+  st.lev1 = (1 << cfg->bits1) - 1;
+  st.lev2 = cfg->bits2 ? (1 << cfg->bits2) - 1 : 0;
+  st.grid2 = (cfg->flags & LVQ_FLAG_LISTING_RESIDUAL) && cfg->bits2 ? 1 : 0;
   st.n_means = cfg->n_means;
   st.metric = cfg->metric;
   st.capacity = cfg->capacity;
-  st.row1 = (int)round_up(ceil_div((int64_t)cfg->d * cfg->bits1, 8), 32);
+  st.row1 = (int)round_up(ceil_div((int64_t)cfg->d * st.bits1, 8), 32);
   st.row2 = cfg->bits2 ? (int)round_up(cfg->d, 32) : 0;
   const int64_t cap = cfg->capacity;
   cudaError_t e = cudaGetDevice(&s->device);
@@ -401,7 +407,7 @@ lvq_status lvq_encode(const lvq_store* s, const float* x, int64_t n, uint8_t* co
   if (n < 0) return fail(s, LVQ_EINVAL, "n < 0");
   if (n == 0) return LVQ_OK;
   if (!x || !codes1 || !lower || !step || !mean_id) return fail(s, LVQ_EINVAL, "null pointer");
-  if (s->ds.bits2 && !codes2) return fail(s, LVQ_EINVAL, "codes2 required when bits2 = 8");
+  if (s->ds.bits2 && !codes2) return fail(s, LVQ_EINVAL, "codes2 required when bits2 > 0");
   if (!valid_stream_device(s)) return fail(s, LVQ_EINVAL, "current device differs from the store's device");
   EncodeOut o;
   o.codes1 = codes1;

@@ -24,7 +24,9 @@
 //                             halves.  8-bit codes: byte j = dim j.  Padding
 //                             bytes are zero.
 //   codes2  [capacity][row2]  residual codes, byte j = dim j, row2 = d rounded
-//                             up to 32 bytes (absent when B2 = 0).
+//                             up to 32 bytes (absent when B2 = 0); unsigned
+//                             on the text's grid, two's complement int8 on
+//                             the listing's signed grid.
 //   lower   [capacity] f32    l(x)
 //   step    [capacity] f32    D
 //   mean_id [capacity] u8     index of the centring mean
@@ -48,7 +50,14 @@ constexpr int kMaxCand = 65536;
 enum : int32_t { kErrNone = 0 };
 
 struct DeviceStore {
+  // bits1 / bits2: the code containers (4- or 8-bit first level, 8-bit
+  // residual bytes or 0) that every scan, gather and re-rank unpacks; b1 /
+  // b2: the quantisers' bit widths (Sec. 3.3: B1 in 2..8, B2 in 2..8), held
+  // in those containers (B1 <= 4 in nibbles, else bytes); lev1 = 2^B1 - 1,
+  // lev2 = 2^B2 - 1; grid2: the residual grid (0 the text's Q_{B2,-D/2,D/2},
+  // 1 the App. C listing's signed grid, step D/2^B2, codes as int8).
   int d, bits1, bits2, n_means, metric;
+  int b1, b2, lev1, lev2, grid2;
   int row1, row2;  // bytes per slot
   int64_t capacity;
   uint8_t* codes1;

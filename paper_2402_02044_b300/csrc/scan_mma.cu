@@ -10,17 +10,20 @@
 // The queries are rounded to float16; the offset is removed afterwards,
 // <q16, c> = acc - 1024 sum(q16).  L2 uses ||q||^2 - 2 <q, x^> + ||x^||^2.
 //
-// One persistent CTA per SM, 14 warps with fixed roles:
+// One persistent CTA per SM, 18 warps with fixed roles:
 //   warp 0      TMA producer: the CTA's query tile (N queries x all dims,
 //               float16, 128-byte swizzle, resident while the CTA works on
 //               that tile) and 128-row x 64-byte boxes of codes (64-byte
 //               swizzle) into a 3-stage ring;
 //   warp 1      allocates TMEM and issues tcgen05.mma (M = 128 database
 //               rows, N queries, K = 16) with A read from TMEM;
-//   warps 2-5   unpack: each thread owns one database row of the tile,
-//               turns 4- or 8-bit codes into float16 pairs and writes them
-//               with tcgen05.st into an A ring in TMEM;
-//   warps 6-13  epilogue (two per TMEM lane quarter, each taking half of the
+//   warps 2-9   unpack, two per TMEM lane quarter taking alternate code
+//               boxes (one box's tcgen05.st completes while the other's
+//               codes are read and converted): each thread owns one
+//               database row of the tile, turns 4- or 8-bit codes into
+//               float16 pairs and writes them with tcgen05.st into an A
+//               ring in TMEM;
+//   warps 10-17 epilogue (two per TMEM lane quarter, each taking half of the
 //               query columns): tcgen05.ld of the float32 accumulators
 //               (double buffered in TMEM) 16 columns at a time, a cheap
 //               per-query filter, then the exact key and the top-k1
@@ -49,8 +52,9 @@ constexpr int kRows = 128;              // database rows per tile (MMA M)
 constexpr int kBoxBytes = 64;           // code bytes per row per TMA box
 constexpr int kStageBytes = kRows * kBoxBytes;
 constexpr int kMaxCodeStages = 16;
-constexpr int kWarps = 14;
-constexpr int kEpiWarp0 = 6;            // first of the 8 epilogue warps
+constexpr int kWarps = 18;
+constexpr int kUnpackWarps = 8;         // warps 2-9
+constexpr int kEpiWarp0 = 2 + kUnpackWarps;  // first of the 8 epilogue warps
 constexpr int kEpiThreads = 256;
 constexpr int kThreads = kWarps * 32;
 constexpr int kTmemCols = 512;
@@ -116,6 +120,20 @@ __device__ __forceinline__ Bars bars_at(uint64_t* b) {
   r.mma_done = r.q_empty + 1;
   return r;
 }
+
+// A position in a ring of n stages: the stage and the parity of its phase,
+// advanced without divisions.
+struct RingPos {
+  int stage = 0;
+  uint32_t phase = 0;
+  __device__ __forceinline__ void advance(int by, int n) {
+    stage += by;
+    while (stage >= n) {
+      stage -= n;
+      phase ^= 1u;
+    }
+  }
+};
 
 // Jobs are dealt round-robin: CTA c takes jobs c, c + grid, ...  At any time
 // the CTAs then work on one or two neighbouring database segments for many
@@ -192,6 +210,7 @@ template <int N, int BITS>
 __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUtensorMap* qmap, const MmaArgs& a,
                                               const Ctx& c) {
   uint32_t ci = 0, qi = 0;
+  RingPos cp;  // code ring position of box ci
   int64_t g_cur = -1;
   for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
     const Job jb = job_of(a, j);
@@ -206,11 +225,12 @@ __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUt
     }
     for (int64_t t = t0; t < t1; ++t) {
       for (int kb = 0; kb < a.n_kbox; ++kb) {
-        const int s = ci % a.code_stages;
-        LVQ_WAIT(c, c.B.code_empty + s, ((ci / a.code_stages) & 1) ^ 1);
+        const int s = cp.stage;
+        LVQ_WAIT(c, c.B.code_empty + s, cp.phase ^ 1);
         mbar_expect_tx(c.B.code_full + s, kStageBytes);
         tma_load_2d(c.cst + s * kStageBytes, cmap, c.B.code_full + s, kb * kBoxBytes, (int)(t * kRows));
         ++ci;
+        cp.advance(1, a.code_stages);
       }
     }
   }
@@ -231,7 +251,8 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
   constexpr int kKSteps = kBoxDims / 16;
   constexpr uint32_t kIdesc = idesc_f16_f32(kRows, N);
   const int AS = a.a_stages;
-  uint32_t ai = 0, di = 0, qi = 0;
+  uint32_t di = 0, qi = 0;
+  RingPos ap;  // A ring position
   int64_t g_cur = -1;
   const uint32_t qbase = smem_u32(c.qs);
   for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
@@ -249,8 +270,8 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
       tc_fence_after();
       const uint32_t d_tmem = c.tbase + db * N;
       for (int kb = 0; kb < a.n_kbox; ++kb) {
-        const int s = ai % AS;
-        LVQ_WAIT(c, c.B.a_full + s, (ai / AS) & 1);
+        const int s = ap.stage;
+        LVQ_WAIT(c, c.B.a_full + s, ap.phase);
         tc_fence_after();
         const uint32_t a_tmem = c.tbase + 2 * N + s * kACols;
         // K step kk of this box reads query dims kg .. kg+15, kg = kb*box + 16kk:
@@ -262,7 +283,7 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
           mma_f16_ts(d_tmem, a_tmem + kk * 8, d0 + off16, kIdesc, (kb | kk) != 0);
         }
         mma_commit(c.B.a_empty + s);
-        ++ai;
+        ap.advance(1, AS);
       }
       mma_commit(c.B.d_full + db);
       ++di;
@@ -283,14 +304,25 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
   const int quarter = warp & 3;
   const int row = quarter * 32 + lane;
   const uint32_t lane_base = c.tbase + ((uint32_t)(quarter * 32) << 16);
-  uint32_t ci = 0, ai = 0;  // boxes seen by the CTA so far
+  // the two warps of a lane quarter take alternate boxes: this warp's boxes
+  // are the CTA's boxes number `parity`, parity + 2, ...
+  const int parity = (warp - 2) >> 2;
+  RingPos cp, ap;  // ring positions of this warp's next box
+  cp.advance(parity, a.code_stages);
+  ap.advance(parity, AS);
+  int skip = parity;  // boxes to pass before this warp's next one
   for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
     const Job jb = job_of(a, j);
     const int64_t t0 = jb.t0, t1 = jb.t1;
     for (int64_t t = t0; t < t1; ++t) {
-      for (int kb = 0; kb < a.n_kbox; ++kb, ++ci, ++ai) {
-        const int s = ci % a.code_stages;
-        LVQ_WAIT(c, c.B.code_full + s, (ci / a.code_stages) & 1);
+      for (int kb = 0; kb < a.n_kbox; ++kb) {
+        if (skip) {
+          --skip;
+          continue;
+        }
+        skip = 1;
+        const int s = cp.stage;
+        LVQ_WAIT(c, c.B.code_full + s, cp.phase);
         const uint4* src = reinterpret_cast<const uint4*>(c.cst + s * kStageBytes + row * kBoxBytes);
         uint4 w[4];
         const int sw = (row >> 1) & 3;  // 64-byte swizzle of the TMA box
@@ -298,19 +330,24 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         for (int q = 0; q < 4; ++q) w[q] = src[q ^ sw];
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.code_empty + s);
-        // both halves in their own registers: tcgen05.st reads its source
-        // registers after issue, so none is rewritten before the wait
-        uint32_t r[32], r2[32];
-        unpack_half<BITS>(w, 0, r);
-        unpack_half<BITS>(w, 1, r2);
-        const int as = ai % AS;
-        LVQ_WAIT(c, c.B.a_empty + as, ((ai / AS) & 1) ^ 1);
+        const int as = ap.stage;
+        LVQ_WAIT(c, c.B.a_empty + as, ap.phase ^ 1);
         tc_fence_after();
         const uint32_t taddr = lane_base + 2 * N + as * kACols;
+        // tcgen05.st reads its source registers after issue: a register set
+        // is rewritten only after tcgen05.wait::st (one set of 32 live at a
+        // time; the other warp of the quarter covers the store latency)
+        uint32_t r[32];
         if (BITS == 4) {
+          unpack_half<BITS>(w, 0, r);
           tmem_st_x32<0>(taddr, r);
-          tmem_st_x32<0>(taddr + 32, r2);
+          tmem_st_wait();
+          unpack_half<BITS>(w, 1, r);
+          tmem_st_x32<0>(taddr + 32, r);
         } else {
+          uint32_t r2[32];
+          unpack_half<BITS>(w, 0, r);
+          unpack_half<BITS>(w, 1, r2);
 #pragma unroll
           for (int i = 0; i < 16; ++i) r[16 + i] = r2[i];
           tmem_st_x32<0>(taddr, r);
@@ -319,6 +356,8 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.a_full + as);
+        cp.advance(2, a.code_stages);
+        ap.advance(2, AS);
       }
     }
   }
@@ -421,8 +460,20 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
     named_bar(1, kEpiThreads);
     if (!c.ep_go[pub++ & 1]) goto out;
     RowMeta nxt = load_meta(a, t0 * kRows + row_in, ip);
+    // The shared bound is read again every tile (the value read one tile ago
+    // is applied, so the load's latency hides behind a tile): once any CTA
+    // has cut a query's buffer, every other CTA filters with the k1-th best
+    // of all rows scanned so far instead of its own.
+    uint64_t pend = kNoKey;
     for (int64_t t = t0; t < t1; ++t) {
       const int db = di & 1;
+      if (et < N && q0 + et < a.nq) {
+        if (pend < c.thr[et]) {
+          c.thr[et] = pend;
+          c.fq[et].z = bound_of(pend, c.qnorm_s[et], c.cmabs_s[et], ip, CM);
+        }
+        pend = *reinterpret_cast<volatile uint64_t*>(a.gthr + q0 + et);
+      }
       if (ew == 0) {
         const bool ok = !*c.abort_sh && mbar_wait(c.B.d_full + db, (di >> 1) & 1, a.wait_limit);
         if (!ok && lane == 0) {
@@ -515,8 +566,9 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
             const int kept = prune_keys(mybuf + n * a.cap, cnt, a.k1, a.k1 + (a.cap - kRows - a.k1) / 2, myhist, &tk);
             if (lane == 0) {
               c.fq[n].w = __int_as_float(kept);
-              c.thr[n] = tk;
-              if (tk != kNoKey) {
+              // the bound only tightens (it may already be the shared one)
+              if (tk < c.thr[n]) {
+                c.thr[n] = tk;
                 atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + q0 + n), tk);
                 c.fq[n].z = bound_of(tk, c.qnorm_s[n], c.cmabs_s[n], ip, CM);
               }

@@ -73,15 +73,43 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// The second level of a slot with step D: its lower bound l2 and step D2,
+// and how its code bytes read as numbers.  The text's grid (Sec. 2.2):
+// l2 = -D/2, D2 = fl(D / (2^B2 - 1)), unsigned codes.  The App. C listing's
+// grid: l2 = 0, D2 = D / 2^B2 (exact), int8 codes, read as excess-128 bytes
+// (XOR 0x80) less 128.
+struct Resid {
+  float lo2, step2;
+  uint32_t flip;
+  float sub;  // 2^23 (+ 128 for signed codes): byte_centred's magic offset
+};
+__device__ __forceinline__ Resid resid_of(const DeviceStore& st, float step) {
+  Resid r;
+  if (st.grid2) {
+    r.lo2 = 0.0f;
+    r.step2 = __fmul_rn(step, __int_as_float((127 - st.b2) << 23));  // step * 2^-B2
+    r.flip = 0x80808080u;
+    r.sub = 8388608.0f + 128.0f;
+  } else {
+    r.lo2 = __fmul_rn(-step, 0.5f);
+    r.step2 = __fdiv_rn(step, (float)st.lev2);
+    r.flip = 0u;
+    r.sub = 8388608.0f;
+  }
+  return r;
+}
+
 // Two-level float32 score of slot s, computed by one warp (result valid in
-// every lane).  x2_j = mu_mj + (l + D c_j) + (l2 + D2 c2_j), l2 = -D/2,
-// D2 = D/255; L2: sum (q_j - x2_j)^2, IP: sum q_j x2_j.  q is in shared memory.
+// every lane).  x2_j = mu_mj + (l + D c_j) + (l2 + D2 c2_j) on the slot's
+// residual grid (resid_of); L2: sum (q_j - x2_j)^2, IP: sum q_j x2_j.  q is
+// in shared memory.
 __device__ __forceinline__ float score2_warp(const DeviceStore& st, int64_t s, const float* qsh) {
   const int lane = threadIdx.x & 31;
   const int d = st.d;
   const int groups = (d + 7) >> 3;
   const float lo = __ldg(st.lower + s), step = __ldg(st.step + s);
-  const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+  const Resid R = resid_of(st, step);
+  const float lo2 = R.lo2, step2 = R.step2;
   const float* mu = st.means + (int64_t)__ldg(st.mean_id + s) * d;
   const uint8_t* row1 = st.codes1 + s * st.row1;
   const uint8_t* row2 = st.codes2 + s * st.row2;
@@ -95,7 +123,7 @@ __device__ __forceinline__ float score2_warp(const DeviceStore& st, int64_t s, c
     for (int e = 0; e < 8; ++e) {
       const int j = g * 8 + e;
       if (j < d) {
-        const float c2 = byte_centred(e < 4 ? w2.x : w2.y, e & 3, 8388608.0f);
+        const float c2 = byte_centred((e < 4 ? w2.x : w2.y) ^ R.flip, e & 3, R.sub);
         const float x2 = __fadd_rn(__fadd_rn(__fmaf_rn(step, c[e], lo), __fmaf_rn(step2, c2, lo2)), __ldg(mu + j));
         if (st.metric == LVQ_L2) {
           const float df = qsh[j] - x2;

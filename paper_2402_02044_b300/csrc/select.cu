@@ -143,7 +143,8 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
       const float lo = __shfl_sync(kFull, lo_l, u), step = __shfl_sync(kFull, st_l, u);
       const int m = __shfl_sync(kFull, m_l, u);
       if (!ok[u]) continue;
-      const float lo2 = __fmul_rn(-step, 0.5f), step2 = __fdiv_rn(step, 255.0f);
+      const Resid R = resid_of(st, step);
+      const float lo2 = R.lo2, step2 = R.step2;
       const float* mu = st.means + (int64_t)m * d;
       const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.row1;
       const uint8_t* r2 = st.codes2 + (int64_t)sid[u] * st.row2;
@@ -156,7 +157,7 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
         for (int e = 0; e < 8; ++e) {
           const int j = g * 8 + e;
           if (j < d) {
-            const float c2 = byte_centred(e < 4 ? b.x : b.y, e & 3, 8388608.0f);
+            const float c2 = byte_centred((e < 4 ? b.x : b.y) ^ R.flip, e & 3, R.sub);
             float x2 = __fadd_rn(__fmaf_rn(step, c[e], lo), __fmaf_rn(step2, c2, lo2));
             if (!one_mean) x2 = __fadd_rn(x2, __ldg(mu + j));
             if (ip) {

@@ -346,17 +346,23 @@ __device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
   return v;
 }
 
-// Approximate pruning of a candidate buffer of n <= 512 distinct keys: find
-// a threshold T among 32 sampled keys such that between k and keep_max keys
+// Forward declaration (defined below): exact select of keys in memory.
+__device__ __forceinline__ int warp_select_mem6(uint64_t* buf, int n, int k, int* hist, uint64_t* thr);
+
+// Approximate pruning of a candidate buffer of n distinct keys: find a
+// threshold T among 32 sampled keys such that between k and keep_max keys
 // are below T, keep those (unsorted) and return their number; *thr = T, a
 // valid insertion threshold (at least k kept keys beat it).  Falls back to
-// the exact select when no sampled key qualifies.  hist: 64 ints.
+// the exact select when no sampled key qualifies.  Up to 512 keys are held
+// in registers; a larger buffer (k1 above 128 gives buffers of 1024) is cut
+// exactly to its k best from memory.  hist: 64 ints.
 __device__ __forceinline__ int warp_prune(uint64_t* buf, int n, int k, int keep_max, int* hist, uint64_t* thr) {
   const int lane = threadIdx.x & 31;
   if (n <= keep_max) {
     *thr = kNoKey;
     return -1;  // nothing to do
   }
+  if (n > 512) return warp_select_mem6(buf, n, k, hist, thr);
   uint64_t v[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) v[e] = e * 32 + lane < n ? buf[e * 32 + lane] : kNoKey;

@@ -29,8 +29,12 @@ PRECISIONS = {"fp32": LVQ_FP32, "fp16": LVQ_FP16_MMA, "auto": LVQ_AUTO, "int16":
 
 class lvq_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("bits1", ctypes.c_int32), ("bits2", ctypes.c_int32),
-                ("n_means", ctypes.c_int32), ("metric", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_means", ctypes.c_int32), ("metric", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("capacity", ctypes.c_int64)]
+
+
+LVQ_FLAG_LISTING_RESIDUAL = 1
+GRIDS = {"text": 0, "listing": LVQ_FLAG_LISTING_RESIDUAL}
 
 
 class lvq_tuning(ctypes.Structure):
@@ -136,9 +140,10 @@ def _ptr(t: Optional[torch.Tensor], dtype, name: str, allow_none: bool = False) 
 # the C ABI, one Python function per entry point
 # --------------------------------------------------------------------------
 
-def lvq_create(d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int) -> int:
+def lvq_create(d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int,
+               grid2: str = "text") -> int:
     means = np.ascontiguousarray(means, dtype=np.float32).reshape(-1, d)
-    cfg = lvq_config(d, bits1, bits2, len(means), METRICS[metric], 0, capacity)
+    cfg = lvq_config(d, bits1, bits2, len(means), METRICS[metric], GRIDS[grid2], capacity)
     out = _P()
     _check(load().lvq_create(ctypes.byref(cfg), means.ctypes.data_as(_P), ctypes.byref(out)), "lvq_create")
     return out.value
@@ -309,10 +314,12 @@ def lvq_last_error(store) -> tuple[int, str]:
 class Store:
     """A device-resident LVQ store (thin wrapper over the C ABI)."""
 
-    def __init__(self, d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int):
+    def __init__(self, d: int, bits1: int, bits2: int, means: np.ndarray, metric: str, capacity: int,
+                 grid2: str = "text"):
         self.d, self.bits1, self.bits2, self.metric, self.capacity = d, bits1, bits2, metric, capacity
+        self.grid2 = grid2
         self.means = np.ascontiguousarray(means, dtype=np.float32).reshape(-1, d)
-        self.handle = lvq_create(d, bits1, bits2, self.means, metric, capacity)
+        self.handle = lvq_create(d, bits1, bits2, self.means, metric, capacity, grid2)
 
     def close(self):
         if self.handle:
@@ -356,6 +363,7 @@ class Store:
         """A handle sharing this store's data with its own scratch memory."""
         v = Store.__new__(Store)
         v.d, v.bits1, v.bits2, v.metric, v.capacity = self.d, self.bits1, self.bits2, self.metric, self.capacity
+        v.grid2 = self.grid2
         v.means = self.means
         v.handle = lvq_store_view(self.handle)
         v._base = self

@@ -14,10 +14,10 @@ def _np(t):
     return t.cpu().numpy() if torch.is_tensor(t) else np.asarray(t)
 
 
-def lib_store(x, means, bits1, bits2, metric, capacity=None):
+def lib_store(x, means, bits1, bits2, metric, capacity=None, grid2="text"):
     from paper_2402_02044_b300 import Store, build
     build.build()
-    st = Store(x.shape[1], bits1, bits2, means, metric, capacity or len(x))
+    st = Store(x.shape[1], bits1, bits2, means, metric, capacity or len(x), grid2=grid2)
     ids = st.insert(torch.from_numpy(np.ascontiguousarray(x)).cuda()) if len(x) else None
     return st, ids
 

@@ -42,12 +42,12 @@ def test_status_strings(lib):
     assert lib.lvq_status_string(3) == b"store full"
 
 
-@pytest.mark.parametrize("field,value", [("d", 0), ("d", 5000), ("bits1", 3), ("bits2", 4), ("n_means", 0),
-                                         ("n_means", 257), ("metric", 2), ("capacity", 0),
-                                         ("capacity", 1 << 31)])
+@pytest.mark.parametrize("field,value", [("d", 0), ("d", 5000), ("bits1", 1), ("bits1", 9), ("bits2", 1),
+                                         ("bits2", 9), ("n_means", 0), ("n_means", 257), ("metric", 2),
+                                         ("flags", 2), ("capacity", 0), ("capacity", 1 << 31)])
 def test_create_rejects_bad_configs_before_touching_the_device(lib, field, value):
     from paper_2402_02044_b300.lvq import lvq_config
-    cfg = dict(d=8, bits1=4, bits2=8, n_means=1, metric=0, reserved=0, capacity=16)
+    cfg = dict(d=8, bits1=4, bits2=8, n_means=1, metric=0, flags=0, capacity=16)
     cfg[field] = value
     c = lvq_config(**cfg)
     means = (ctypes.c_float * (8 * 300))()

@@ -125,3 +125,23 @@ def test_fp16_and_fp32_paths_both_match_the_oracle():
         assert abs(O.recall_at_k(gi.cpu().numpy(), truth, 10) - O.recall_at_k(ref_i, truth, 10)) <= 0.01, prec
     check_no_device_error(st)
     st.close()
+
+
+@pytest.mark.parametrize("k1", [200, 512])
+def test_large_k1_with_full_candidate_buffers(k1):
+    """k1 above 128 gives per-(CTA, query) candidate buffers of 1024 keys;
+    with few CTAs each scans thousands of rows, so the buffers fill and are
+    cut many times: no candidate may be lost in a cut (every first-level
+    and two-level result equals the oracle's)."""
+    x, q, means = gmm_case(30000, 96, 16, "l2", 24, seed=131 + k1)
+    st, ids = lib_store(x, means, 4, 8, "l2")
+    enc = O.encode(x, means, 4, 8)
+    qt = torch.from_numpy(q).cuda()
+    for ctas in (7, 0):
+        st.set_tuning(mma_ctas=ctas)
+        fi, fs = st.first_level(qt, k1, "fp16")
+        check_topk_ids(q, fi, fs, enc, means, "l2", k1, TOL_FP16, level=1)
+        gi, gs = st.search(qt, 10, k1, "fp16")
+        check_two_level(q, gi, gs, (fi, fs), enc, means, "l2", k1, 10, TOL_FP16)
+    check_no_device_error(st)
+    st.close()

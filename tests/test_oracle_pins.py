@@ -29,7 +29,7 @@ def _cases():
 def test_hand_worked_encodings(case):
     x = np.array([case["x"]], dtype=F32)
     means = np.array(case["means"], dtype=F32)
-    enc = O.encode(x, means, case["bits1"], case["bits2"])
+    enc = O.encode(x, means, case["bits1"], case["bits2"], grid2=case.get("grid2", "text"))
     assert enc["mean_id"][0] == case["mean_id"]
     assert enc["lower"][0] == F32(case["lower"])
     assert enc["step"][0] == F32(case["step"])
@@ -48,7 +48,7 @@ def test_hand_worked_quantisation_errors(case):
     # centre dropped on both sides or a missing residual term all fail here.
     x = np.array([case["x"]], dtype=F32)
     means = np.array(case["means"], dtype=F32)
-    enc = O.encode(x, means, case["bits1"], case["bits2"])
+    enc = O.encode(x, means, case["bits1"], case["bits2"], grid2=case.get("grid2", "text"))
     assert O.eps_first(x, means, enc) == pytest.approx(case["eps1"], rel=1e-12, abs=1e-300)
     assert O.eps_second(x, means, enc) == pytest.approx(case["eps2"], rel=1e-12, abs=1e-300)
 
@@ -106,6 +106,38 @@ def test_residual_level_tightens_error():
     assert np.all(np.abs(r - rhat) <= step2[:, None] / 2 + slack[:, None])
     e1, e2 = O.eps_first(x, mu[None], enc), O.eps_second(x, mu[None], enc)
     assert e2 < e1 / 100
+
+
+@pytest.mark.parametrize("bits1,bits2,grid2", [(2, 8, "text"), (3, 8, "text"), (5, 4, "text"), (6, 2, "text"),
+                                               (7, 3, "text"), (8, 2, "text"), (4, 8, "listing"),
+                                               (8, 2, "listing"), (3, 5, "listing")])
+def test_other_widths_code_ranges_and_error_bounds(bits1, bits2, grid2):
+    # Sec. 3.3 (B1, B2 heatmap) and App. C: for every width the first-level
+    # codes lie in [0, 2^B1 - 1] and err by at most D/2; the residual codes
+    # lie on their grid and err by at most D2/2 (text grid) or D2/2 inside the
+    # signed grid's range and D2 at its clipped top (listing grid); the two
+    # levels together err less than the first level alone.
+    x, mu = _gmm(n=1500)
+    enc = O.encode(x, mu[None], bits1, bits2, grid2=grid2)
+    assert enc["codes1"].max() <= (1 << bits1) - 1 and enc["codes1"].min() >= 0
+    y = x.astype(np.float64) - mu.astype(np.float64)[None]
+    x1 = O.decode_first(enc, mu[None]) - mu.astype(np.float64)[None]
+    slack = np.spacing(np.abs(y).max(axis=1).astype(F32)).astype(np.float64)[:, None] * 8
+    assert np.all(np.abs(y - x1) <= enc["step"][:, None] / 2 + slack)
+    r = y - x1
+    lower2, step2 = O.residual_grid(enc["step"], bits2, grid2)
+    c2 = enc["codes2"].astype(np.int64)
+    rhat = lower2.astype(np.float64)[:, None] + step2.astype(np.float64)[:, None] * c2
+    if grid2 == "text":
+        assert c2.min() >= 0 and c2.max() <= (1 << bits2) - 1
+        assert np.all(np.abs(r - rhat) <= step2[:, None] / 2 + slack)
+    else:
+        half = 1 << (bits2 - 1)
+        assert c2.min() >= -half and c2.max() <= half - 1
+        # r lies in [-D/2, D/2] = [-half D2, half D2]: only the top code clips
+        bound = np.where(c2 == half - 1, step2[:, None], step2[:, None] / 2)
+        assert np.all(np.abs(r - rhat) <= bound + slack)
+    assert O.eps_second(x, mu[None], enc) < O.eps_first(x, mu[None], enc)
 
 
 def test_uniform_quantiser_mean_square_error():
