@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
     } else {
       const int64_t s = out.slots[v];
       if (s < 0) continue;
-      uint32_t* row1 = reinterpret_cast<uint32_t*>(st.codes1 + s * st.row1);
+      uint32_t* row1 = reinterpret_cast<uint32_t*>(st.codes1 + s * st.stride1);
       const int words1 = st.row1 >> 2;
 #pragma unroll
       for (int i = 0; i < WPL; ++i) {
@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(256) encode_kernel(DeviceStore st, const float
         st.step[s] = step;
         st.mean_id[s] = (uint8_t)m_star;
         st.norm2[s] = nrm;
+        // the record's trailer: the same constants beside the codes
+        *reinterpret_cast<uint4*>(st.codes1 + s * st.stride1 + st.row1) =
+            make_uint4(__float_as_uint(lo), __float_as_uint(step), __float_as_uint(nrm), (uint32_t)m_star);
       }
     }
   }
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(256) export_kernel(DeviceStore st, const int64
     for (int j = lane; j < d; j += 32) {
       uint32_t c = 0, r = 0;
       if (ok) {
-        const uint8_t* row = st.codes1 + s * st.row1;
+        const uint8_t* row = st.codes1 + s * st.stride1;
         if (st.bits1 == 4) {
           const uint32_t w = reinterpret_cast<const uint32_t*>(row)[j >> 3];
           const int e = j & 7;
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(DeviceStore st, const 
   const float lo = st.lower[s], step = st.step[s];
   const float lo2 = st.grid2 ? 0.0f : __fmul_rn(-step, 0.5f);
   const float step2 = st.grid2 ? __fmul_rn(step, __int_as_float((127 - st.b2) << 23)) : __fdiv_rn(step, (float)st.lev2);
-  const uint8_t* r1 = st.codes1 + s * st.row1;
+  const uint8_t* r1 = st.codes1 + s * st.stride1;
   const uint8_t* r2 = st.bits2 ? st.codes2 + s * st.row2 : nullptr;
   for (int j = lane; j < st.d; j += 32) {
     uint32_t c;

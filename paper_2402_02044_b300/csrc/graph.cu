@@ -29,7 +29,7 @@ __device__ __forceinline__ float score1_warp(const DeviceStore& st, int64_t s, c
   const int groups = (d + 7) >> 3;
   const float lo = __ldg(st.lower + s), step = __ldg(st.step + s);
   const float* mu = st.means + (int64_t)__ldg(st.mean_id + s) * d;
-  const uint8_t* row1 = st.codes1 + s * st.row1;
+  const uint8_t* row1 = st.codes1 + s * st.stride1;
   float acc = 0.0f;
   for (int g = lane; g < groups; g += 32) {
     float c[8];

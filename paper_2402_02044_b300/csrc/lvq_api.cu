@@ -327,7 +327,8 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   st.n_means = cfg->n_means;
   st.metric = cfg->metric;
   st.capacity = cfg->capacity;
-  st.row1 = (int)round_up(ceil_div((int64_t)cfg->d * st.bits1, 8), 32);
+  st.row1 = (int)round_up(ceil_div((int64_t)cfg->d * st.bits1, 8), 16);
+  st.stride1 = st.row1 + 16;
   st.row2 = cfg->bits2 ? (int)round_up(cfg->d, 32) : 0;
   const int64_t cap = cfg->capacity;
   cudaError_t e = cudaGetDevice(&s->device);
@@ -335,7 +336,7 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   auto A = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16);
   };
-  A((void**)&st.codes1, (size_t)cap * st.row1);
+  A((void**)&st.codes1, (size_t)cap * st.stride1);
   if (st.bits2) A((void**)&st.codes2, (size_t)cap * st.row2);
   A((void**)&st.lower, (size_t)cap * 4);
   A((void**)&st.step, (size_t)cap * 4);
@@ -350,7 +351,7 @@ lvq_status lvq_create(const lvq_config* cfg, const float* means_host, lvq_store*
   if (e == cudaSuccess) e = cudaMemset(st.reserved, 0, (size_t)round_up(ceil_div(cap, 32) * 4, 16));
   if (e == cudaSuccess) e = cudaMemset(st.err, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(s->counters, 0, kCtrWords * 8);
-  if (e == cudaSuccess) e = cudaMemset(st.codes1, 0, (size_t)cap * st.row1);
+  if (e == cudaSuccess) e = cudaMemset(st.codes1, 0, (size_t)cap * st.stride1);
   if (e == cudaSuccess) e = cudaMemcpy(st.means, means_host, (size_t)cfg->n_means * cfg->d * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {

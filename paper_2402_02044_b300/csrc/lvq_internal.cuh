@@ -14,9 +14,14 @@
 // ---------------------------------------------------------------------------
 // Store layout in HBM (structure of arrays, one entry per slot)
 //
-//   codes1  [capacity][row1]  first-level codes.  row1 = ceil(d*B1/8) rounded
-//                             up to 32 bytes (the paper pads LVQ records to
-//                             multiples of 32 B).  4-bit codes: 32-bit word w
+//   codes1  [capacity][stride1] one record per slot: row1 bytes of
+//                             first-level codes (row1 = ceil(d*B1/8) rounded
+//                             up to 16 bytes), then a 16-byte trailer
+//                             {l, D, ||x^1||^2 as float32, mean id as u32},
+//                             a copy of the per-vector constants below, so
+//                             that a gather of one slot reads one record
+//                             (stride1 = row1 + 16: 64 B at d = 96 with 4-bit
+//                             codes, the paper's padded record size).  4-bit codes: 32-bit word w
 //                             holds dims 8w..8w+7 with dim 8w+2p in bits
 //                             4p..4p+3 and dim 8w+2p+1 in bits 16+4p..19+4p
 //                             (p = 0..3), so (word >> 4p) & 0x000F000F puts
@@ -58,7 +63,8 @@ struct DeviceStore {
   // 1 the App. C listing's signed grid, step D/2^B2, codes as int8).
   int d, bits1, bits2, n_means, metric;
   int b1, b2, lev1, lev2, grid2;
-  int row1, row2;  // bytes per slot
+  int row1, row2;  // code bytes per slot (first level, residual)
+  int stride1;     // bytes per first-level record: row1 + 16-byte trailer
   int64_t capacity;
   uint8_t* codes1;
   uint8_t* codes2;

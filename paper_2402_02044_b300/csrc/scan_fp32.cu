@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) scan_fp32_kernel(Fp32Args a) {
     for (int64_t tile = t_begin; tile < t_end; ++tile) {
       const int64_t row = tile * kThreads + tid;
       if (row < a.plan.n_rows && is_live(st.live, row)) {
-        const uint4* codes = reinterpret_cast<const uint4*>(st.codes1 + row * st.row1);
+        const uint4* codes = reinterpret_cast<const uint4*>(st.codes1 + row * st.stride1);
         const float lo = __ldg(st.lower + row), step = __ldg(st.step + row);
         const int m = __ldg(st.mean_id + row);
         const float* mu = st.means + (int64_t)m * st.d;

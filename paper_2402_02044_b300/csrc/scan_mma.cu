@@ -750,7 +750,7 @@ cudaError_t encode_code_map(const DeviceStore& st, CUtensorMap* cm, int box_byte
   if (!enc) return cudaErrorNotSupported;
   if (box_bytes != 64 && box_bytes != 128) return cudaErrorInvalidValue;
   cuuint64_t dims[2] = {(cuuint64_t)st.row1, (cuuint64_t)st.capacity};
-  cuuint64_t strides[1] = {(cuuint64_t)st.row1};
+  cuuint64_t strides[1] = {(cuuint64_t)st.stride1};  // records: codes, then a 16-byte trailer
   cuuint32_t box[2] = {(cuuint32_t)box_bytes, (cuuint32_t)kRows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(cm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, st.codes1, dims, strides, box, es,

@@ -111,7 +111,7 @@ __device__ __forceinline__ float score2_warp(const DeviceStore& st, int64_t s, c
   const Resid R = resid_of(st, step);
   const float lo2 = R.lo2, step2 = R.step2;
   const float* mu = st.means + (int64_t)__ldg(st.mean_id + s) * d;
-  const uint8_t* row1 = st.codes1 + s * st.row1;
+  const uint8_t* row1 = st.codes1 + s * st.stride1;
   const uint8_t* row2 = st.codes2 + s * st.row2;
   float acc = 0.0f;
   for (int g = lane; g < groups; g += 32) {

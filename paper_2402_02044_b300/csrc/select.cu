@@ -128,7 +128,7 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
     uint2 w1[kRU][kRG], w2[kRU][kRG];
 #pragma unroll
     for (int u = 0; u < kRU; ++u) {
-      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.row1;
+      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.stride1;
       const uint8_t* r2 = st.codes2 + (int64_t)sid[u] * st.row2;
 #pragma unroll
       for (int gi = 0; gi < kRG; ++gi) {
@@ -146,7 +146,7 @@ __device__ void rerank_tail(const DeviceStore& st, float* qsh, const uint64_t* k
       const Resid R = resid_of(st, step);
       const float lo2 = R.lo2, step2 = R.step2;
       const float* mu = st.means + (int64_t)m * d;
-      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.row1;
+      const uint8_t* r1 = st.codes1 + (int64_t)sid[u] * st.stride1;
       const uint8_t* r2 = st.codes2 + (int64_t)sid[u] * st.row2;
       float acc = 0.0f;
       auto add_group = [&](uint2 a, uint2 b, int g) {
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
         const int row = (int)__umulhi((uint32_t)c, r16_magic), col = c - row * r16;
         const bool in = c < R * r16;
         const int64_t sr = __shfl_sync(kFull, s, in ? row : 0);
-        if (in && sr >= 0) cp_async16(base + (size_t)row * gg.stride + 16 * col, st.codes1 + sr * st.row1 + 16 * col);
+        if (in && sr >= 0) cp_async16(base + (size_t)row * gg.stride + 16 * col, st.codes1 + sr * st.stride1 + 16 * col);
       }
       ++i_n;
       if (++i_rd == per_q) {
@@ -661,6 +661,187 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   cp_async_wait<0>();
 }
 
+// ---- ID-gather search with the query in registers (d <= 768) -----------------
+// One query at a time per 128-thread block (persistent blocks).  A row is
+// scored by L consecutive lanes (a power of two); lane l owns the 8-dim code
+// groups l, l + L, .., at most three, and holds the query's four byte planes
+// for those groups in registers for the whole query, so a row costs its code
+// words (read straight from HBM into registers, lanes of a row reading
+// consecutive words) and dp4a, with no shared-memory traffic for the query.
+// Each record's 16-byte trailer (l, D, ||x^||^2, mean id) comes with it, so
+// a candidate is one record read.  Each warp keeps P steps of R = 32 / L rows
+// in flight (loads for step t + P issued as step t is scored).  The exact
+// integer products and the score follow the fixed-point scheme above.
+constexpr int kG2Threads = 128;
+constexpr int kG2Warps = kG2Threads / 32;
+constexpr int kG2Steps = 4;  // steps of R rows each warp keeps in flight
+
+__host__ __device__ inline int pow2_ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+template <int GL, int BITS>
+__global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
+                                                             QueryPrep p, const int64_t* __restrict__ cand, int n_cand,
+                                                             int k, int L, int cap, int64_t* out_ids,
+                                                             float* out_scores) {
+  constexpr int P = kG2Steps;
+  constexpr int WPG = BITS == 4 ? 1 : 2;  // code words per 8-dim group
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* buf = reinterpret_cast<uint64_t*>(smem);  // [cap]
+  int* sh_pos = reinterpret_cast<int*>(buf + cap);    // [k + 2]
+  __shared__ int cnt;
+  __shared__ uint64_t thr;
+  __shared__ int scan_sh[kG2Warps + 1];
+  __shared__ float qmax_sh[kG2Warps];
+  __shared__ long long qsum_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d = st.d, W = (d + 7) >> 3;
+  const int R = 32 / L;
+  const int r = lane / L, l = lane % L;
+  const bool ip = st.metric == LVQ_IP;
+  const long long ioff = BITS == 4 ? 8 : 128;
+  const float off = BITS == 4 ? 8.0f : 128.0f;
+  const int per_round = kG2Warps * P * R;  // rows a round of the block scores
+  const int rounds = (n_cand + per_round - 1) / per_round;
+  for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+    const float* qrow = q + qi * d;
+    float mx = 0.0f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) mx = fmaxf(mx, fabsf(qrow[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    if (lane == 0) qmax_sh[warp] = mx;
+    if (threadIdx.x == 0) {
+      cnt = 0;
+      thr = kNoKey;
+    }
+    __syncthreads();
+    mx = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kG2Warps; ++i) mx = fmaxf(mx, qmax_sh[i]);
+    const int qe = mx > 0.0f ? ilogbf(mx) - 30 : 0;
+    const float qscale = mx > 0.0f ? ldexpf(1.0f, qe) : 0.0f;
+    // this lane's planes: pw[i][plane][half] for group l + L i
+    uint32_t pw[GL][4][2];
+    long long part = 0;
+#pragma unroll
+    for (int i = 0; i < GL; ++i) {
+      const int g = l + L * i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        pw[i][0][h] = pw[i][1][h] = pw[i][2][h] = pw[i][3][h] = 0u;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = 8 * g + plane_dim(BITS, h, b);
+          const int v = (g < W && j < d) ? max(-2147483647, __float2int_rn(ldexpf(qrow[j], -qe))) : 0;
+          part += v;
+          pw[i][0][h] |= (uint32_t)(v & 255) << (8 * b);
+          pw[i][1][h] |= (uint32_t)((v >> 8) & 255) << (8 * b);
+          pw[i][2][h] |= (uint32_t)((v >> 16) & 255) << (8 * b);
+          pw[i][3][h] |= (uint32_t)((v >> 24) & 255) << (8 * b);
+        }
+      }
+    }
+    // sum of the rounded query over all dims: the lanes of row 0 of warp 0
+    // hold every group once
+    if (warp == 0) {
+      if (r != 0) part = 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+      if (lane == 0) qsum_sh = part;
+    }
+    __syncthreads();
+    const long long qoff = qsum_sh * ioff;
+    const float qs = p.qsum[qi];
+    const float qn = ip ? 0.0f : p.qnorm[qi];
+    const float* cmq = p.cm + qi * st.n_means;
+    // the candidate rows of this warp's step t: s = kG2Warps t + warp, rows s R + r
+    uint32_t cw[P][GL * WPG];
+    uint4 tr[P];
+    uint32_t lv[P];
+    int sid[P];
+    auto load_step = [&](int t, uint32_t(&cwu)[GL * WPG], uint4& tru, uint32_t& lvu, int& sidu) {
+      const int i = (kG2Warps * t + warp) * R + r;
+      int id = -1;
+      if (i < n_cand) {
+        const int64_t c = __ldg(cand + qi * n_cand + i);
+        if (c >= 0 && c < st.capacity) id = (int)c;
+      }
+      sidu = id;
+      const uint8_t* rec = st.codes1 + (int64_t)(id < 0 ? 0 : id) * st.stride1;
+#pragma unroll
+      for (int gi = 0; gi < GL; ++gi) {
+        const int g = l + L * gi;
+        const bool in = id >= 0 && g < W;
+        if (BITS == 4) {
+          cwu[gi] = in ? __ldg(reinterpret_cast<const uint32_t*>(rec) + g) : 0u;
+        } else {
+          const uint2 v = in ? __ldg(reinterpret_cast<const uint2*>(rec) + g) : make_uint2(0u, 0u);
+          cwu[2 * gi] = v.x;
+          cwu[2 * gi + 1] = v.y;
+        }
+      }
+      tru = make_uint4(0u, 0u, 0u, 0u);
+      lvu = 0u;
+      if (l == 0 && id >= 0) {
+        tru = __ldg(reinterpret_cast<const uint4*>(rec + st.row1));
+        lvu = __ldg(st.live + (id >> 5));
+      }
+    };
+#pragma unroll
+    for (int u = 0; u < P; ++u) load_step(u, cw[u], tr[u], lv[u], sid[u]);
+    for (int rd = 0; rd < rounds; ++rd) {
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        GatherAcc A = {0u, 0u, 0u, 0};
+#pragma unroll
+        for (int gi = 0; gi < GL; ++gi) {
+          const uint32_t x0 = BITS == 4 ? (cw[u][gi] & 0x0F0F0F0Fu) : cw[u][WPG * gi];
+          const uint32_t x1 = BITS == 4 ? ((cw[u][gi] >> 4) & 0x0F0F0F0Fu) : cw[u][WPG * gi + WPG - 1];
+          plane_step(A, x0, x1, make_uint2(pw[gi][0][0], pw[gi][0][1]), make_uint2(pw[gi][1][0], pw[gi][1][1]),
+                     make_uint2(pw[gi][2][0], pw[gi][2][1]), make_uint2(pw[gi][3][0], pw[gi][3][1]));
+        }
+        long long dot = (long long)A.a0 + ((long long)A.a1 << 8) + ((long long)A.a2 << 16) + ((long long)A.a3 << 24);
+        for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
+        const uint4 t4 = tr[u];
+        const int id = sid[u];
+        const bool live = id >= 0 && ((lv[u] >> (id & 31)) & 1u);
+        // refill this slot with step t + P while the row is scored
+        load_step((rd + 1) * P + u, cw[u], tr[u], lv[u], sid[u]);
+        if (l == 0 && live) {
+          const float lo = __uint_as_float(t4.x), stp = __uint_as_float(t4.y), nrm = __uint_as_float(t4.z);
+          const int m = (int)t4.w;
+          const float a = __fmul_rn(qscale, (float)(dot - qoff));
+          float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo), qs, cmq[m]));
+          if (!ip) sc = __fadd_rn(__fadd_rn(qn, nrm), -2.0f * sc);
+          const uint64_t key = make_key(sc, (uint32_t)id, st.metric);
+          if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
+        }
+      }
+      __syncthreads();
+      if (cnt > cap - per_round) {
+        uint64_t t;
+        const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
+        if (threadIdx.x == 0) {
+          cnt = kept;
+          thr = t;
+        }
+        __syncthreads();
+      }
+    }
+    {
+      uint64_t t;
+      const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
+      if (threadIdx.x == 0) cnt = kept;
+      __syncthreads();
+    }
+    write_results(buf, cnt, k, st.metric, out_ids + qi * k, out_scores + qi * k, sh_pos);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_prep_queries(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
@@ -746,10 +927,69 @@ GatherGeom gather_geom(int row1, int d, int k) {
   return g;  // does not fit: the launcher refuses it
 }
 
+// Lanes per row and groups per lane of gather2_kernel: the fewest lane slots
+// (L a power of two, at most three groups a lane), ties to more groups a
+// lane (fewer shuffles); {0, 0} when a row would need more than 8 lanes.
+// Measured on B300: at d = 96 (L = 4, eight rows a warp step) it beats the
+// shared-memory ring kernel (0.83 vs 1.16 ms for 8,192 x 2,048 ids); at
+// d = 768 (L = 32, one row a step) the per-row shuffles and loads cost more
+// than the ring kernel's plane reads (0.74 vs 0.43 ms for 1,024 x 2,048).
+static void gather2_shape(int d, int* L, int* GL) {
+  const int W = (d + 7) / 8;
+  *L = 0;
+  *GL = 0;
+  int best = 1 << 30;
+  for (int gl = 3; gl >= 1; --gl) {
+    const int l = pow2_ceil((W + gl - 1) / gl);
+    if (l <= 8 && l * gl < best) {
+      best = l * gl;
+      *L = l;
+      *GL = gl;
+    }
+  }
+}
+
+template <int GL, int BITS>
+static cudaError_t launch_gather2_t(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
+                                    const int64_t* cand, int n_cand, int k, int L, int64_t* out_ids,
+                                    float* out_scores, cudaStream_t stream) {
+  const int per_round = kG2Warps * kG2Steps * (32 / L);
+  const int cap = pow2_at_least(k + 2 * per_round);
+  const size_t smem = (size_t)cap * 8 + (size_t)(k + 2) * 4 + 16;
+  static std::atomic<uint64_t> attr{0};
+  {
+    const cudaError_t e = max_dyn_smem_once((const void*)gather2_kernel<GL, BITS>, 200 * 1024, attr);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather2_kernel<GL, BITS>, kG2Threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t grid = std::min<int64_t>(nq, (int64_t)sms * per_sm);
+  gather2_kernel<GL, BITS><<<(unsigned)grid, kG2Threads, smem, stream>>>(st, q, nq, p, cand, n_cand, k, L, cap,
+                                                                           out_ids, out_scores);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                           const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
                           cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
+  int L = 0, GL = 0;
+  gather2_shape(st.d, &L, &GL);
+  if (GL > 0 && (st.bits1 == 4 || st.bits1 == 8)) {
+    const bool b4 = st.bits1 == 4;
+    switch (GL) {
+      case 1: return b4 ? launch_gather2_t<1, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
+                        : launch_gather2_t<1, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
+      case 2: return b4 ? launch_gather2_t<2, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
+                        : launch_gather2_t<2, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
+      default: return b4 ? launch_gather2_t<3, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
+                         : launch_gather2_t<3, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
+    }
+  }
+  // wider rows: the shared-memory ring kernel
   const GatherGeom g = gather_geom(st.row1, st.d, k);
   if (g.smem > kGatherSmemBudget) return cudaErrorInvalidValue;
   static std::atomic<uint64_t> attr{0};
