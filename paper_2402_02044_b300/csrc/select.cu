@@ -276,8 +276,12 @@ __global__ void __launch_bounds__(T) merge_rerank_kernel(DeviceStore st, const f
         if (pass) buf[at + __popc(m & ((1u << lane) - 1u))] = v[r];
       }
     }
+    // every thread reads the count before any starts the next round's
+    // appends, so all take the same branch
     __syncthreads();
-    if (cnt > cap - kMergeRound) {
+    const int c_now = cnt;
+    __syncthreads();
+    if (c_now > cap - kMergeRound) {
       uint64_t tk;
       const int kept = cut_keys<T>(buf, cap, cnt, k1, hist, scan_sh, &tk);
       if (threadIdx.x == 0) {
@@ -637,8 +641,12 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
           __syncwarp();
         }
       }
+      // every thread reads the count before any starts the next round's
+      // appends, so all take the same branch
       __syncthreads();
-      if (cnt > cap - kGatherThreads) {
+      const int c_now = cnt;
+      __syncthreads();
+      if (c_now > cap - kGatherThreads) {
         uint64_t t;
         const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
         if (threadIdx.x == 0) {
@@ -669,12 +677,17 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
 // words (read straight from HBM into registers, lanes of a row reading
 // consecutive words) and dp4a, with no shared-memory traffic for the query.
 // Each record's 16-byte trailer (l, D, ||x^||^2, mean id) comes with it, so
-// a candidate is one record read.  Each warp keeps P steps of R = 32 / L rows
-// in flight (loads for step t + P issued as step t is scored).  The exact
+// a candidate is one record read (lane l of a row loads trailer word l, so a
+// row's four lanes hold it in one register each).  Each warp keeps P steps of
+// R = 32 / L rows in flight (loads for step t + P issued as step t is
+// scored).  The exact
 // integer products and the score follow the fixed-point scheme above.
 constexpr int kG2Threads = 128;
 constexpr int kG2Warps = kG2Threads / 32;
-constexpr int kG2Steps = 4;  // steps of R rows each warp keeps in flight
+#ifndef LVQ_G2_STEPS
+#define LVQ_G2_STEPS 4
+#endif
+constexpr int kG2Steps = LVQ_G2_STEPS;  // steps of R rows each warp keeps in flight
 
 __host__ __device__ inline int pow2_ceil(int v) {
   int p = 1;
@@ -759,17 +772,22 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
     const float* cmq = p.cm + qi * st.n_means;
     // the candidate rows of this warp's step t: s = kG2Warps t + warp, rows s R + r
     uint32_t cw[P][GL * WPG];
-    uint4 tr[P];
+    uint32_t tw[P];  // trailer word l of the row
     uint32_t lv[P];
-    int sid[P];
-    auto load_step = [&](int t, uint32_t(&cwu)[GL * WPG], uint4& tru, uint32_t& lvu, int& sidu) {
+    int sid[P];      // slot of the row whose record is in flight
+    int nid[P];      // slot of the row one round later (its id read a round ahead)
+    // a step's candidate id (-1: skipped); ids are read a round before the
+    // records they address, so no record load waits on an id load
+    auto load_id = [&](int t) -> int {
       const int i = (kG2Warps * t + warp) * R + r;
       int id = -1;
       if (i < n_cand) {
         const int64_t c = __ldg(cand + qi * n_cand + i);
         if (c >= 0 && c < st.capacity) id = (int)c;
       }
-      sidu = id;
+      return id;
+    };
+    auto load_rec = [&](int id, uint32_t(&cwu)[GL * WPG], uint32_t& twu, uint32_t& lvu) {
       const uint8_t* rec = st.codes1 + (int64_t)(id < 0 ? 0 : id) * st.stride1;
 #pragma unroll
       for (int gi = 0; gi < GL; ++gi) {
@@ -783,15 +801,16 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
           cwu[2 * gi + 1] = v.y;
         }
       }
-      tru = make_uint4(0u, 0u, 0u, 0u);
-      lvu = 0u;
-      if (l == 0 && id >= 0) {
-        tru = __ldg(reinterpret_cast<const uint4*>(rec + st.row1));
-        lvu = __ldg(st.live + (id >> 5));
-      }
+      twu = (l < 4 && id >= 0) ? __ldg(reinterpret_cast<const uint32_t*>(rec + st.row1) + l) : 0u;
+      lvu = (l == 0 && id >= 0) ? __ldg(st.live + (id >> 5)) : 0u;
     };
 #pragma unroll
-    for (int u = 0; u < P; ++u) load_step(u, cw[u], tr[u], lv[u], sid[u]);
+    for (int u = 0; u < P; ++u) sid[u] = load_id(u);
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      load_rec(sid[u], cw[u], tw[u], lv[u]);
+      nid[u] = load_id(P + u);
+    }
     for (int rd = 0; rd < rounds; ++rd) {
 #pragma unroll
       for (int u = 0; u < P; ++u) {
@@ -805,11 +824,16 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
         }
         long long dot = (long long)A.a0 + ((long long)A.a1 << 8) + ((long long)A.a2 << 16) + ((long long)A.a3 << 24);
         for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
-        const uint4 t4 = tr[u];
+        const int rb = lane - l;  // the row's first lane
+        const uint4 t4 = make_uint4(__shfl_sync(kFull, tw[u], rb), __shfl_sync(kFull, tw[u], rb + 1),
+                                    __shfl_sync(kFull, tw[u], rb + 2), __shfl_sync(kFull, tw[u], rb + 3));
         const int id = sid[u];
         const bool live = id >= 0 && ((lv[u] >> (id & 31)) & 1u);
-        // refill this slot with step t + P while the row is scored
-        load_step((rd + 1) * P + u, cw[u], tr[u], lv[u], sid[u]);
+        // refill this slot with step t + P (its id is already here) while the
+        // row is scored, and read the id of step t + 2 P
+        sid[u] = nid[u];
+        load_rec(sid[u], cw[u], tw[u], lv[u]);
+        nid[u] = load_id((rd + 2) * P + u);
         if (l == 0 && live) {
           const float lo = __uint_as_float(t4.x), stp = __uint_as_float(t4.y), nrm = __uint_as_float(t4.z);
           const int m = (int)t4.w;
@@ -820,8 +844,12 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
           if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
         }
       }
+      // every thread reads the count before any starts the next round's
+      // appends, so all take the same branch
       __syncthreads();
-      if (cnt > cap - per_round) {
+      const int c_now = cnt;
+      __syncthreads();
+      if (c_now > cap - per_round) {
         uint64_t t;
         const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
         if (threadIdx.x == 0) {
@@ -929,7 +957,8 @@ GatherGeom gather_geom(int row1, int d, int k) {
 
 // Lanes per row and groups per lane of gather2_kernel: the fewest lane slots
 // (L a power of two, at most three groups a lane), ties to more groups a
-// lane (fewer shuffles); {0, 0} when a row would need more than 8 lanes.
+// lane (fewer shuffles); {0, 0} when a row would need more than 8 lanes or
+// fewer than 4 (the four trailer words are spread over a row's lanes).
 // Measured on B300: at d = 96 (L = 4, eight rows a warp step) it beats the
 // shared-memory ring kernel (0.83 vs 1.16 ms for 8,192 x 2,048 ids); at
 // d = 768 (L = 32, one row a step) the per-row shuffles and loads cost more
@@ -941,7 +970,7 @@ static void gather2_shape(int d, int* L, int* GL) {
   int best = 1 << 30;
   for (int gl = 3; gl >= 1; --gl) {
     const int l = pow2_ceil((W + gl - 1) / gl);
-    if (l <= 8 && l * gl < best) {
+    if (l >= 4 && l <= 8 && l * gl < best) {
       best = l * gl;
       *L = l;
       *GL = gl;
