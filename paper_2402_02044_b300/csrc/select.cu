@@ -367,6 +367,19 @@ __device__ __forceinline__ int g_dp4a_us(uint32_t a, uint32_t b, int c) {
   asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
+// Read-only loads of a record's words that ask L2 to fetch only the 64-byte
+// half line the word is in: a randomly addressed 64-byte record then costs 64
+// bytes of DRAM traffic, not a whole 128-byte line.
+__device__ __forceinline__ uint32_t ldg_half_line(const uint32_t* p) {
+  uint32_t v;
+  asm("ld.global.nc.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ldg_half_line(const uint2* p) {
+  uint2 v;
+  asm("ld.global.nc.L2::64B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
 
 // Dim (within its group of 8) of byte b of the query word that meets code
 // bytes in dp4a: for 4-bit codes half h = 0 pairs with (w & 0x0F0F0F0F),
@@ -695,11 +708,10 @@ __host__ __device__ inline int pow2_ceil(int v) {
   return p;
 }
 
-template <int GL, int BITS>
+template <int GL, int BITS, int L>
 __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
                                                              QueryPrep p, const int64_t* __restrict__ cand, int n_cand,
-                                                             int k, int L, int cap, int64_t* out_ids,
-                                                             float* out_scores) {
+                                                             int k, int cap, int64_t* out_ids, float* out_scores) {
   constexpr int P = kG2Steps;
   constexpr int WPG = BITS == 4 ? 1 : 2;  // code words per 8-dim group
   extern __shared__ __align__(16) unsigned char smem[];
@@ -712,7 +724,7 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
   __shared__ long long qsum_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = st.d, W = (d + 7) >> 3;
-  const int R = 32 / L;
+  constexpr int R = 32 / L;
   const int r = lane / L, l = lane % L;
   const bool ip = st.metric == LVQ_IP;
   const long long ioff = BITS == 4 ? 8 : 128;
@@ -794,14 +806,14 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
         const int g = l + L * gi;
         const bool in = id >= 0 && g < W;
         if (BITS == 4) {
-          cwu[gi] = in ? __ldg(reinterpret_cast<const uint32_t*>(rec) + g) : 0u;
+          cwu[gi] = in ? ldg_half_line(reinterpret_cast<const uint32_t*>(rec) + g) : 0u;
         } else {
-          const uint2 v = in ? __ldg(reinterpret_cast<const uint2*>(rec) + g) : make_uint2(0u, 0u);
+          const uint2 v = in ? ldg_half_line(reinterpret_cast<const uint2*>(rec) + g) : make_uint2(0u, 0u);
           cwu[2 * gi] = v.x;
           cwu[2 * gi + 1] = v.y;
         }
       }
-      twu = (l < 4 && id >= 0) ? __ldg(reinterpret_cast<const uint32_t*>(rec + st.row1) + l) : 0u;
+      twu = (l < 4 && id >= 0) ? ldg_half_line(reinterpret_cast<const uint32_t*>(rec + st.row1) + l) : 0u;
       lvu = (l == 0 && id >= 0) ? __ldg(st.live + (id >> 5)) : 0u;
     };
 #pragma unroll
@@ -822,8 +834,18 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
           plane_step(A, x0, x1, make_uint2(pw[gi][0][0], pw[gi][0][1]), make_uint2(pw[gi][1][0], pw[gi][1][1]),
                      make_uint2(pw[gi][2][0], pw[gi][2][1]), make_uint2(pw[gi][3][0], pw[gi][3][1]));
         }
-        long long dot = (long long)A.a0 + ((long long)A.a1 << 8) + ((long long)A.a2 << 16) + ((long long)A.a3 << 24);
-        for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(kFull, dot, o);
+        // planes 0 + 1 and 2 + 3 in 32 bits each, exactly: with c <= 2^B1 - 1
+        // and d <= 192 (at most 24 groups of 8 dims), the first pair is at
+        // most d (2^B1 - 1) 255 257 < 2^32 (unsigned) and the second (plane 3
+        // signed) at most d (2^B1 - 1) (255 + 128 256) < 2^31 in magnitude
+        uint32_t lo = A.a0 + (A.a1 << 8);
+        int hi = (int)A.a2 + (A.a3 << 8);
+#pragma unroll
+        for (int o = L >> 1; o > 0; o >>= 1) {
+          lo += __shfl_xor_sync(kFull, lo, o);
+          hi += __shfl_xor_sync(kFull, hi, o);
+        }
+        const long long dot = (long long)lo + ((long long)hi << 16);
         const int rb = lane - l;  // the row's first lane
         const uint4 t4 = make_uint4(__shfl_sync(kFull, tw[u], rb), __shfl_sync(kFull, tw[u], rb + 1),
                                     __shfl_sync(kFull, tw[u], rb + 2), __shfl_sync(kFull, tw[u], rb + 3));
@@ -978,26 +1000,26 @@ static void gather2_shape(int d, int* L, int* GL) {
   }
 }
 
-template <int GL, int BITS>
+template <int GL, int BITS, int L>
 static cudaError_t launch_gather2_t(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
-                                    const int64_t* cand, int n_cand, int k, int L, int64_t* out_ids,
-                                    float* out_scores, cudaStream_t stream) {
+                                    const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
+                                    cudaStream_t stream) {
   const int per_round = kG2Warps * kG2Steps * (32 / L);
   const int cap = pow2_at_least(k + 2 * per_round);
   const size_t smem = (size_t)cap * 8 + (size_t)(k + 2) * 4 + 16;
   static std::atomic<uint64_t> attr{0};
   {
-    const cudaError_t e = max_dyn_smem_once((const void*)gather2_kernel<GL, BITS>, 200 * 1024, attr);
+    const cudaError_t e = max_dyn_smem_once((const void*)gather2_kernel<GL, BITS, L>, 200 * 1024, attr);
     if (e != cudaSuccess) return e;
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather2_kernel<GL, BITS>, kG2Threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather2_kernel<GL, BITS, L>, kG2Threads, smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t grid = std::min<int64_t>(nq, (int64_t)sms * per_sm);
-  gather2_kernel<GL, BITS><<<(unsigned)grid, kG2Threads, smem, stream>>>(st, q, nq, p, cand, n_cand, k, L, cap,
-                                                                           out_ids, out_scores);
+  gather2_kernel<GL, BITS, L><<<(unsigned)grid, kG2Threads, smem, stream>>>(st, q, nq, p, cand, n_cand, k, cap,
+                                                                              out_ids, out_scores);
   return cudaGetLastError();
 }
 
@@ -1008,15 +1030,23 @@ cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, con
   int L = 0, GL = 0;
   gather2_shape(st.d, &L, &GL);
   if (GL > 0 && (st.bits1 == 4 || st.bits1 == 8)) {
-    const bool b4 = st.bits1 == 4;
-    switch (GL) {
-      case 1: return b4 ? launch_gather2_t<1, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
-                        : launch_gather2_t<1, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
-      case 2: return b4 ? launch_gather2_t<2, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
-                        : launch_gather2_t<2, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
-      default: return b4 ? launch_gather2_t<3, 4>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream)
-                         : launch_gather2_t<3, 8>(st, q, nq, p, cand, n_cand, k, L, out_ids, out_scores, stream);
+    const int sel = (GL - 1) * 4 + (st.bits1 == 4 ? 0 : 2) + (L == 4 ? 0 : 1);
+#define LVQ_G2(gl, b, l) launch_gather2_t<gl, b, l>(st, q, nq, p, cand, n_cand, k, out_ids, out_scores, stream)
+    switch (sel) {
+      case 0: return LVQ_G2(1, 4, 4);
+      case 1: return LVQ_G2(1, 4, 8);
+      case 2: return LVQ_G2(1, 8, 4);
+      case 3: return LVQ_G2(1, 8, 8);
+      case 4: return LVQ_G2(2, 4, 4);
+      case 5: return LVQ_G2(2, 4, 8);
+      case 6: return LVQ_G2(2, 8, 4);
+      case 7: return LVQ_G2(2, 8, 8);
+      case 8: return LVQ_G2(3, 4, 4);
+      case 9: return LVQ_G2(3, 4, 8);
+      case 10: return LVQ_G2(3, 8, 4);
+      default: return LVQ_G2(3, 8, 8);
     }
+#undef LVQ_G2
   }
   // wider rows: the shared-memory ring kernel
   const GatherGeom g = gather_geom(st.row1, st.d, k);
