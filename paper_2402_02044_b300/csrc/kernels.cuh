@@ -104,7 +104,7 @@ cudaError_t launch_small_prep(const DeviceStore& st, const float* q, int64_t nq,
 cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep& p, const void* scratch,
                               const ScanPlan& plan, cudaStream_t stream);
 // persistent CTAs of the small-batch scan: one per SM, at most one per tile
-int small_grid(int64_t n_rows, int sm_count);
+int small_grid(const DeviceStore& st, int64_t n_rows, int64_t nq, int k1, int sm_count);
 
 // ---- greedy beam search over a graph (graph.cu) --------------------------------
 // slots of the seen-set (power of two, at most half full) and shared memory

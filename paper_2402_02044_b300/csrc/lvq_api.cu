@@ -147,7 +147,7 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, int64_t n_row
     groups = sc.prep.nq_pad / sc.n_tile;
   } else if (path == kPathSmall) {
     sc.small = c.take<unsigned char>(small_scratch_bytes(st, nq));
-    grid = small_grid(n_rows, s->sm_count);
+    grid = small_grid(st, n_rows, nq, k1, s->sm_count);
     tiles_rows = 128;
     groups = 1;
   } else {

@@ -11,15 +11,18 @@
 // (2, 6, 3, 7); the query bytes are stored in the same order.  Then
 //   IP: s = <q, mu_m> + l sum(q) + D <q, c>;   L2: ||q||^2 + ||x^||^2 - 2 s.
 //
-// One persistent CTA per SM scans a contiguous range of 128-row database
-// tiles.  One thread of warp 0 streams each tile's 128-byte code boxes with
-// TMA into one of two rings (even tiles, odd tiles); warps 1-4 and
-// 5-8 are two groups of 128 threads, one row per thread, that take the even
-// and the odd tiles and run without waiting for each other.  Per query and
-// group, scores below a running threshold (the lower of the two groups')
-// go to a candidate buffer in shared memory, which a warp cuts back to the
-// k1 best when it fills; at the end each CTA's k1 best of the union go to
-// partial[q][cta][.].
+// One persistent CTA per SM scans a contiguous range of database tiles.
+// One thread of warp 0 streams each tile's 128-byte code boxes with TMA into
+// one ring per consumer group; each group (four warps, 128 threads) takes
+// every G-th tile and runs without waiting for the others.  A thread scores
+// one row of a 128-row tile, or, when the batch has two or more queries, two
+// rows of a 256-row tile: the query bytes come from shared memory (a 128-bit
+// broadcast read costs four shared-memory wavefronts, which bound the scan
+// once there are several queries), and each read then serves two rows.  Per
+// query and group, scores below a running threshold (the lowest of the
+// groups') go to a candidate buffer in shared memory, which a warp cuts back
+// to the k1 best when it fills; at the end each CTA's k1 best of the union go
+// to partial[q][cta][.].
 #include <cudaTypedefs.h>
 
 #include "kernels.cuh"
@@ -82,10 +85,10 @@ struct SmallSmem {
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 // cand: [QB][G groups][cap] keys; thr, cnt: [G][QB]; hist: 64 ints per consumer warp
-__host__ __device__ inline SmallSmem small_layout(int qb, int G, int Wp, int M, int cap, int stages) {
+__host__ __device__ inline SmallSmem small_layout(int qb, int G, int Wp, int M, int cap, int stages, int rpt) {
   SmallSmem s;
   s.ring = 0;
-  s.qw = s.ring + G * stages * kStageBytes;
+  s.qw = s.ring + G * stages * kStageBytes * rpt;
   s.fq = s.qw + qb * 4 * Wp * 4;
   s.thr = s.fq + qb * 16;
   s.cnt = s.thr + G * qb * 8;
@@ -97,17 +100,21 @@ __host__ __device__ inline SmallSmem small_layout(int qb, int G, int Wp, int M, 
   return s;
 }
 
-// QB: query slots (nq <= QB); BITS: first-level code width; G: consumer groups
-template <int QB, int BITS, int G>
+// QB: query slots (nq <= QB); BITS: first-level code width; G: consumer
+// groups; RPT: rows per consumer thread (a tile is RPT x 128 rows, thread i
+// of a group scores rows i, i + 128, .. of it).
+template <int QB, int BITS, int G, int RPT>
 __global__ void __launch_bounds__(small_threads(G), 1)
     scan_small_kernel(const __grid_constant__ CUtensorMap cmap, SmallArgs a) {
   constexpr int kThreads = small_threads(G);
+  constexpr int kTR = kRows * RPT;              // rows per tile
+  constexpr int kStageB = kStageBytes * RPT;    // bytes per ring stage (RPT boxes)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const DeviceStore& st = a.st;
   const int RS = a.stages;
-  const SmallSmem L = small_layout(QB, G, a.Wp, st.n_means, a.cap, RS);
+  const SmallSmem L = small_layout(QB, G, a.Wp, st.n_means, a.cap, RS, RPT);
   unsigned char* ring = smem + L.ring;
   uint32_t* qw = reinterpret_cast<uint32_t*>(smem + L.qw);
   float4* fq = reinterpret_cast<float4*>(smem + L.fq);  // {sum q, s, 0, ||q||^2}
@@ -179,8 +186,11 @@ __global__ void __launch_bounds__(small_threads(G), 1)
           const uint32_t ci = fills[g];
           const int s = g * RS + (int)(ci % RS);
           if (!mbar_test_wait(empty + s, ((ci / RS) & 1) ^ 1)) continue;
-          mbar_expect_tx(full + s, kStageBytes);
-          tma_load_2d(ring + s * kStageBytes, &cmap, full + s, next_kb[g] * kBoxBytes, (int)(next_t[g] * kRows));
+          mbar_expect_tx(full + s, kStageB);
+#pragma unroll
+          for (int pr = 0; pr < RPT; ++pr)
+            tma_load_2d(ring + s * kStageB + pr * kStageBytes, &cmap, full + s, next_kb[g] * kBoxBytes,
+                        (int)(next_t[g] * kTR + pr * kRows));
           fills[g] = ci + 1;
           if (++next_kb[g] == a.n_kbox) {
             next_kb[g] = 0;
@@ -224,22 +234,33 @@ __global__ void __launch_bounds__(small_threads(G), 1)
       if (go) {
         // four independent accumulator chains per query: A/B halves (4-bit)
         // or even/odd words (8-bit), high and low query bytes
-        int hi[QB][2];
-        uint32_t lo[QB][2];
+        int hi[RPT][QB][2];
+        uint32_t lo[RPT][QB][2];
 #pragma unroll
-        for (int q = 0; q < QB; ++q) {
-          hi[q][0] = hi[q][1] = 0;
-          lo[q][0] = lo[q][1] = 0u;
-        }
-        // per-row constants and the live bit, all loaded now and first used
+        for (int pr = 0; pr < RPT; ++pr)
+#pragma unroll
+          for (int q = 0; q < QB; ++q) {
+            hi[pr][q][0] = hi[pr][q][1] = 0;
+            lo[pr][q][0] = lo[pr][q][1] = 0u;
+          }
+        // per-row constants and the live bits, all loaded now and first used
         // after the boxes (no load waits on another)
-        const int64_t rw = t * kRows + row;
-        const bool in_range = rw < a.n_rows;
-        const int64_t ms = in_range ? rw : 0;
-        const uint32_t live_w = __ldg(st.live + (ms >> 5));
-        const float lo_r = __ldg(st.lower + ms), step_r = __ldg(st.step + ms);
-        const int m_r = __ldg(st.mean_id + ms);
-        const float nrm = ip ? 0.0f : __ldg(st.norm2 + ms);
+        int64_t rw[RPT];
+        bool in_range[RPT];
+        uint32_t live_w[RPT];
+        float lo_r[RPT], step_r[RPT], nrm[RPT];
+        int m_r[RPT];
+#pragma unroll
+        for (int pr = 0; pr < RPT; ++pr) {
+          rw[pr] = t * kTR + pr * kRows + row;
+          in_range[pr] = rw[pr] < a.n_rows;
+          const int64_t ms = in_range[pr] ? rw[pr] : 0;
+          live_w[pr] = __ldg(st.live + (ms >> 5));
+          lo_r[pr] = __ldg(st.lower + ms);
+          step_r[pr] = __ldg(st.step + ms);
+          m_r[pr] = __ldg(st.mean_id + ms);
+          nrm[pr] = ip ? 0.0f : __ldg(st.norm2 + ms);
+        }
         for (int kb = 0; kb < a.n_kbox; ++kb, ++used) {
           const int s = g * RS + (int)(used % RS);
           if (!mbar_wait(full + s, (used / RS) & 1, kWaitLimit)) {
@@ -250,15 +271,18 @@ __global__ void __launch_bounds__(small_threads(G), 1)
             go = false;
             break;
           }
-          const uint4* src = reinterpret_cast<const uint4*>(ring + s * kStageBytes + row * kBoxBytes);
-          uint4 w[kChunks];
+          uint4 w[RPT][kChunks];
 #pragma unroll
-          for (int c = 0; c < kChunks; ++c) w[c] = src[c ^ sw];
+          for (int pr = 0; pr < RPT; ++pr) {
+            const uint4* src =
+                reinterpret_cast<const uint4*>(ring + s * kStageB + pr * kStageBytes + row * kBoxBytes);
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) w[pr][c] = src[c ^ sw];
+          }
           __syncwarp();
           if (lane == 0) mbar_arrive(empty + s);
 #pragma unroll
           for (int c = 0; c < kChunks; ++c) {
-            const uint32_t ws[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
             const int word0 = kb * (kBoxBytes / 4) + c * 4;
 #pragma unroll
             for (int q = 0; q < QB; ++q) {
@@ -273,41 +297,52 @@ __global__ void __launch_bounds__(small_threads(G), 1)
                 const uint32_t bhs[4] = {bh.x, bh.y, bh.z, bh.w};
                 const uint32_t bls[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                  const uint32_t A = ws[i] & 0x0F0F0F0Fu;
-                  const uint32_t B = (ws[i] >> 4) & 0x0F0F0F0Fu;
-                  hi[q][0] = dp4a_us(A, ahs[i], hi[q][0]);
-                  hi[q][1] = dp4a_us(B, bhs[i], hi[q][1]);
-                  lo[q][0] = dp4a_uu(A, als[i], lo[q][0]);
-                  lo[q][1] = dp4a_uu(B, bls[i], lo[q][1]);
+                for (int pr = 0; pr < RPT; ++pr) {
+                  const uint32_t ws[4] = {w[pr][c].x, w[pr][c].y, w[pr][c].z, w[pr][c].w};
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) {
+                    const uint32_t A = ws[i] & 0x0F0F0F0Fu;
+                    const uint32_t B = (ws[i] >> 4) & 0x0F0F0F0Fu;
+                    hi[pr][q][0] = dp4a_us(A, ahs[i], hi[pr][q][0]);
+                    hi[pr][q][1] = dp4a_us(B, bhs[i], hi[pr][q][1]);
+                    lo[pr][q][0] = dp4a_uu(A, als[i], lo[pr][q][0]);
+                    lo[pr][q][1] = dp4a_uu(B, bls[i], lo[pr][q][1]);
+                  }
                 }
               } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                  hi[q][i & 1] = dp4a_us(ws[i], ahs[i], hi[q][i & 1]);
-                  lo[q][i & 1] = dp4a_uu(ws[i], als[i], lo[q][i & 1]);
+                for (int pr = 0; pr < RPT; ++pr) {
+                  const uint32_t ws[4] = {w[pr][c].x, w[pr][c].y, w[pr][c].z, w[pr][c].w};
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) {
+                    hi[pr][q][i & 1] = dp4a_us(ws[i], ahs[i], hi[pr][q][i & 1]);
+                    lo[pr][q][i & 1] = dp4a_uu(ws[i], als[i], lo[pr][q][i & 1]);
+                  }
                 }
               }
             }
           }
         }
-        const bool valid = in_range && ((live_w >> (ms & 31)) & 1u);
-        if (go && valid) {
 #pragma unroll
-          for (int q = 0; q < QB; ++q) {
-            if (q < a.nq) {
-              const float4 f = fq[q];
-              const float h = (float)(hi[q][0] + hi[q][1]);
-              const float l = (float)lo[q][0] + (float)lo[q][1];
-              const float dot = f.y * __fmaf_rn(256.0f, h, l);
-              float sc = __fmaf_rn(step_r, dot, __fmaf_rn(lo_r, f.x, cmt[q * M + m_r]));
-              if (!ip) sc = f.w + nrm - 2.0f * sc;
-              const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
-              // every group's threshold bounds the CTA's k1-th best
-              uint64_t tq = thr[q];
+        for (int pr = 0; pr < RPT; ++pr) {
+          const bool valid = in_range[pr] && ((live_w[pr] >> (rw[pr] & 31)) & 1u);
+          if (go && valid) {
 #pragma unroll
-              for (int h = 1; h < G; ++h) tq = thr[h * QB + q] < tq ? thr[h * QB + q] : tq;
-              if (key < tq) cand[(q * G + g) * cap + atomicAdd(&my_cnt[q], 1)] = key;
+            for (int q = 0; q < QB; ++q) {
+              if (q < a.nq) {
+                const float4 f = fq[q];
+                const float h = (float)(hi[pr][q][0] + hi[pr][q][1]);
+                const float l = (float)lo[pr][q][0] + (float)lo[pr][q][1];
+                const float dot = f.y * __fmaf_rn(256.0f, h, l);
+                float sc = __fmaf_rn(step_r[pr], dot, __fmaf_rn(lo_r[pr], f.x, cmt[q * M + m_r[pr]]));
+                if (!ip) sc = f.w + nrm[pr] - 2.0f * sc;
+                const uint64_t key = make_key(sc, (uint32_t)rw[pr], st.metric);
+                // every group's threshold bounds the CTA's k1-th best
+                uint64_t tq = thr[q];
+#pragma unroll
+                for (int h = 1; h < G; ++h) tq = thr[h * QB + q] < tq ? thr[h * QB + q] : tq;
+                if (key < tq) cand[(q * G + g) * cap + atomicAdd(&my_cnt[q], 1)] = key;
+              }
             }
           }
         }
@@ -317,7 +352,7 @@ __global__ void __launch_bounds__(small_threads(G), 1)
       if (wq < QB && wq < a.nq) {
         // a buffer without room for another tile is cut to the k1 best, whose
         // k1-th key bounds every CTA's search
-        if (my_cnt[wq] > cap - kRows) {
+        if (my_cnt[wq] > cap - kTR) {
           uint64_t tk;
           const int kept = select_k(cand + (wq * G + g) * cap, my_cnt[wq], a.k1, hist + cw * 64, &tk);
           if (lane == 0) {
@@ -420,29 +455,39 @@ __global__ void __launch_bounds__(256) small_prep_kernel(DeviceStore st, const f
   }
 }
 
-template <int QB, int BITS, int G>
+template <int QB, int BITS, int G, int RPT>
 cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_t smem, cudaStream_t stream) {
   static std::atomic<uint64_t> attr{0};
-  const cudaError_t e = max_dyn_smem_once((const void*)scan_small_kernel<QB, BITS, G>, kSmemLimit, attr);
+  const cudaError_t e = max_dyn_smem_once((const void*)scan_small_kernel<QB, BITS, G, RPT>, kSmemLimit, attr);
   if (e != cudaSuccess) return e;
-  scan_small_kernel<QB, BITS, G><<<grid, small_threads(G), smem, stream>>>(cm, a);
+  scan_small_kernel<QB, BITS, G, RPT><<<grid, small_threads(G), smem, stream>>>(cm, a);
   return cudaGetLastError();
 }
 
-int small_cap(int k1) { return pow2_at_least(k1 + 2 * kRows); }
+int small_cap(int k1, int rpt) { return pow2_at_least(k1 + 2 * kRows * rpt); }
 int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
 int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
 // consumer groups: more warps hide more load latency, while the registers of
-// more queries allow fewer of them (4, 3 and 2 groups for 1, 2 and 4 slots)
-int small_groups(int qb) { return qb <= 1 ? 4 : qb <= 2 ? 3 : 2; }
+// more queries allow fewer of them (4, 3 and 2 groups for 1, 2 and 4 slots;
+// two when each thread takes two rows)
+int small_groups(int qb, int rpt) { return rpt == 2 ? 2 : qb <= 1 ? 4 : qb <= 2 ? 3 : 2; }
 
 // ring stages per ring: as many as shared memory holds, up to kMaxRingStages;
 // 0 when not even two fit
-int small_stages(const DeviceStore& st, int qb, int k1) {
-  const int G = small_groups(qb);
+int small_stages(const DeviceStore& st, int qb, int k1, int rpt) {
+  const int G = small_groups(qb, rpt);
   for (int rs = kMaxRingStages; rs >= 2; --rs)
-    if (small_layout(qb, G, small_wp(st), st.n_means, small_cap(k1), rs).total + 1024 <= kSmemLimit) return rs;
+    if (small_layout(qb, G, small_wp(st), st.n_means, small_cap(k1, rpt), rs, rpt).total + 1024 <= kSmemLimit)
+      return rs;
   return 0;
+}
+
+// rows per consumer thread: with one query each code word meets one query
+// word either way; with more, two rows per thread halve the query words read
+// from shared memory per row (when the larger buffers and stages fit)
+int small_rpt(const DeviceStore& st, int64_t nq, int k1) {
+  const int qb = small_qb(nq);
+  return qb >= 2 && small_stages(st, qb, k1, 2) > 0 ? 2 : 1;
 }
 
 }  // namespace
@@ -451,7 +496,7 @@ bool small_supported(const DeviceStore& st, int64_t nq, int k1) {
   if (nq < 1 || nq > kSmallMaxQ || k1 < 1 || k1 > 1024) return false;
   if (st.bits1 != 4 && st.bits1 != 8) return false;
   if (!mma_supported(st)) return false;  // needs the CUDA driver's tensor-map encoder too
-  return small_stages(st, small_qb(nq), k1) > 0;
+  return small_stages(st, small_qb(nq), k1, small_rpt(st, nq, k1)) > 0;
 }
 
 // scratch: rounded queries [nq][4][Wp] u32 | scales [nq] f32 | global bounds [nq] u64 (8-byte aligned)
@@ -463,8 +508,8 @@ static uint64_t* small_gthr(void* scratch, const DeviceStore& st, int64_t nq) {
   return reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + off);
 }
 
-int small_grid(int64_t n_rows, int sm_count) {
-  const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, kRows);
+int small_grid(const DeviceStore& st, int64_t n_rows, int64_t nq, int k1, int sm_count) {
+  const int64_t ntiles = ceil_div(n_rows > 0 ? n_rows : 1, (int64_t)kRows * small_rpt(st, nq, k1));
   return (int)(ntiles < sm_count ? ntiles : sm_count);
 }
 
@@ -492,26 +537,34 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
   a.qscale = reinterpret_cast<const float*>(qw + nq * 4 * a.Wp);
   a.n_kbox = (int)ceil_div(st.row1, kBoxBytes);
   a.k1 = plan.k1;
-  a.cap = small_cap(plan.k1);
+  const int qb = small_qb(nq), rpt = small_rpt(st, nq, plan.k1);
+  a.cap = small_cap(plan.k1, rpt);
   a.n_rows = plan.n_rows;
-  a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, kRows);
+  a.ntiles = ceil_div(plan.n_rows > 0 ? plan.n_rows : 1, (int64_t)kRows * rpt);
   a.partial = plan.partial;
   a.counts = plan.counts;
   a.gthr = small_gthr(const_cast<void*>(scratch), st, nq);
   if (!a.counts) return cudaErrorInvalidValue;
-  const int qb = small_qb(nq);
-  a.stages = small_stages(st, qb, plan.k1);
+  a.stages = small_stages(st, qb, plan.k1, rpt);
   if (a.stages == 0) return cudaErrorInvalidValue;
   CUtensorMap cm;
   cudaError_t e = encode_code_map(st, &cm, kBoxBytes);
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)small_layout(qb, small_groups(qb), a.Wp, st.n_means, a.cap, a.stages).total + 1024;
+  const size_t smem =
+      (size_t)small_layout(qb, small_groups(qb, rpt), a.Wp, st.n_means, a.cap, a.stages, rpt).total + 1024;
   const int grid = plan.grid;
   const bool b4 = st.bits1 == 4;
   switch (qb) {
-    case 1: return b4 ? launch_qb<1, 4, 4>(cm, a, grid, smem, stream) : launch_qb<1, 8, 4>(cm, a, grid, smem, stream);
-    case 2: return b4 ? launch_qb<2, 4, 3>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3>(cm, a, grid, smem, stream);
-    default: return b4 ? launch_qb<4, 4, 2>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2>(cm, a, grid, smem, stream);
+    case 1:
+      return b4 ? launch_qb<1, 4, 4, 1>(cm, a, grid, smem, stream) : launch_qb<1, 8, 4, 1>(cm, a, grid, smem, stream);
+    case 2:
+      if (rpt == 2)
+        return b4 ? launch_qb<2, 4, 2, 2>(cm, a, grid, smem, stream) : launch_qb<2, 8, 2, 2>(cm, a, grid, smem, stream);
+      return b4 ? launch_qb<2, 4, 3, 1>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3, 1>(cm, a, grid, smem, stream);
+    default:
+      if (rpt == 2)
+        return b4 ? launch_qb<4, 4, 2, 2>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2, 2>(cm, a, grid, smem, stream);
+      return b4 ? launch_qb<4, 4, 2, 1>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2, 1>(cm, a, grid, smem, stream);
   }
 }
 
