@@ -73,6 +73,10 @@ struct ScanPlan {
   int grid;             // persistent CTAs
   int* counts = nullptr;  // [nq][splits] valid keys per list (null: lists padded with kNoKey)
   uint64_t* gthr = nullptr;  // [nq] per-query bound shared by the CTAs of the tensor-core scan
+  // tensor-core scan: [nq][splits][best_j] lowest keys of disjoint row sets
+  // (rows of one segment, id mod best_j); best_j = 0 leaves them out
+  uint64_t* seg_best = nullptr;
+  int best_j = 0;
   uint32_t wait_polls = 0;   // polls of each pipeline wait of the tensor-core scan (0: the default)
 };
 constexpr int kMaxMergeLists = 1024;  // lists per query when counts are given

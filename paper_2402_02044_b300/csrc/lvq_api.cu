@@ -183,6 +183,14 @@ size_t plan_scan(const lvq_store* s, int64_t nq, int k1, int path, int64_t n_row
   sc.plan.partial = c.take<uint64_t>((size_t)nq * splits * k1);
   sc.plan.counts = path != kPathFp32 ? c.take<int>((size_t)nq * splits) : nullptr;
   sc.plan.gthr = mma ? c.take<uint64_t>((size_t)nq) : nullptr;
+  if (mma) {
+    // enough keys of distinct rows per query that their k1-th lowest can bound
+    // the search: ceil(k1 / segments) per segment, at most 256 per query (the
+    // bound warp runs with query tiles of up to 64)
+    const int j = (int)ceil_div(k1, splits);
+    sc.plan.best_j = (int64_t)splits * j <= 256 && sc.n_tile <= 64 ? j : 0;
+    sc.plan.seg_best = sc.plan.best_j ? c.take<uint64_t>((size_t)nq * splits * sc.plan.best_j) : nullptr;
+  }
   const size_t cand = mma                  ? mma_scan_cand_bytes(sc.plan.grid, sc.n_tile, k1)
                      : path == kPathSmall ? 0
                                           : fp32_scan_cand_bytes(sc.plan.grid, sc.qb, k1);

@@ -10,7 +10,7 @@
 // The queries are rounded to float16; the offset is removed afterwards,
 // <q16, c> = acc - 1024 sum(q16).  L2 uses ||q||^2 - 2 <q, x^> + ||x^||^2.
 //
-// One persistent CTA per SM, 18 warps with fixed roles:
+// One persistent CTA per SM, 18 or 19 warps with fixed roles:
 //   warp 0      TMA producer: the CTA's query tile (N queries x all dims,
 //               float16, 128-byte swizzle, resident while the CTA works on
 //               that tile) and 128-row x 64-byte boxes of codes (64-byte
@@ -27,10 +27,21 @@
 //               query columns): tcgen05.ld of the float32 accumulators
 //               (double buffered in TMEM) 16 columns at a time, a cheap
 //               per-query filter, then the exact key and the top-k1
-//               threshold test for the few rows that pass it.
+//               threshold test for the few rows that pass it;
+//   warp 18     (query tiles of up to 64) bound: lowers each query's
+//               shared bound (below).
 // Work is a list of jobs (a query tile x a database segment), dealt evenly
 // between the CTAs; a CTA's stretch of one query tile is a "segment" whose
 // k1 best keys go to partial[q][segment].
+//
+// The filter's bound for a query is the lowest of (a) its own buffer's
+// k1-th key, (b) the shared per-query bound, which every CTA lowers to its
+// buffer's k1-th key when it cuts the buffer, and (c) a union bound: every
+// exact key also lowers, in global memory, the lowest key of its (segment,
+// id mod J) row set, J = ceil(k1 / segments); the bound warp takes the k1-th
+// lowest of a query's segments x J such keys, all of distinct rows, so at
+// least k1 rows lie at or below it.  Unlike (a) and (b), which stand for one
+// CTA's share of the rows, (c) stands for all rows scanned so far.
 //
 // Every wait on an mbarrier is bounded; on expiry the CTA records
 // LVQ_ETIMEOUT, stops issuing work, waits (bounded) for its own copies and
@@ -52,11 +63,19 @@ constexpr int kRows = 128;              // database rows per tile (MMA M)
 constexpr int kBoxBytes = 64;           // code bytes per row per TMA box
 constexpr int kStageBytes = kRows * kBoxBytes;
 constexpr int kMaxCodeStages = 16;
-constexpr int kWarps = 18;
+// the bound warp runs with query tiles of up to 64 (measured on B300: it
+// makes 16- and 64-query scans 1.2x and 1.6x faster, while a full 128-query
+// tile is held up by a 19th warp even when it idles, and its own bound
+// rarely beats the segments' by then)
+template <int N>
+constexpr int warps_of() {
+  return N <= 64 ? 19 : 18;
+}
 constexpr int kUnpackWarps = 8;         // warps 2-9
 constexpr int kEpiWarp0 = 2 + kUnpackWarps;  // first of the 8 epilogue warps
+constexpr int kBoundWarp = kEpiWarp0 + 8;       // the bound warp
 constexpr int kEpiThreads = 256;
-constexpr int kThreads = kWarps * 32;
+
 constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
@@ -83,6 +102,8 @@ struct MmaArgs {
   int segs;           // database segments (equal ranges of tiles)
   int64_t jobs;       // groups x segs; job j = (query tile j % groups, segment j / groups)
   uint32_t wait_limit;  // polls of a pipeline wait before the CTA gives up (drains use kWaitLimit)
+  uint64_t* seg_best;   // [nq][segs][best_j]: lowest key of the rows of a segment with id = i mod best_j
+  int best_j;           // 0: no such keys kept
 };
 
 struct Smem {
@@ -192,6 +213,7 @@ struct Ctx {
   __half* cm16;     // [N][M] <q, mu_m> in float16, or null
   float* cm32;      // [N][M] <q, mu_m> in float32, or null
   volatile int* ep_go;  // [2] epilogue leader's verdicts, read by the 4 epilogue warps after a named barrier
+  volatile int* bw_job;  // the epilogue's current job for the bound warp (-1 none yet, -2 finished)
   int cta, grid;
 };
 
@@ -397,6 +419,33 @@ __device__ __forceinline__ float bound_of(uint64_t tk, float qn, float cmabs, bo
   return b;
 }
 
+// A bound on the k-th lowest key of a query from the lowest keys of P <= 256
+// disjoint row sets (kNoKey where a set has none): the smallest score word
+// T such that at least k of the P keys have a score word <= T, as the key
+// (T, any id).  At least k distinct rows then have keys at or below it, so
+// the query's k-th lowest key over all rows is too.  kNoKey when fewer than
+// k keys exist.  Called by a whole warp.
+__device__ __noinline__ uint64_t union_bound(const uint64_t* keys, int P, int k, int lane) {
+  uint32_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int at = lane + 32 * i;
+    v[i] = at < P ? (uint32_t)(__ldcg(keys + at) >> 32) : 0xFFFFFFFFu;
+  }
+  uint32_t lo = 0, hi = 0xFFFFFFFFu;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    int c = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c += v[i] <= mid ? 1 : 0;
+    if ((int)__reduce_add_sync(kFull, (unsigned)c) >= k)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo == 0xFFFFFFFFu ? kNoKey : (((uint64_t)lo << 32) | 0xFFFFFFFFull);
+}
+
 // Candidate-buffer selections, kept out of line: they run rarely and their
 // register arrays would otherwise share the epilogue's register budget.
 __device__ __noinline__ int prune_keys(uint64_t* buf, int n, int k, int keep_max, int* hist, uint64_t* thr) {
@@ -432,6 +481,7 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
     const Job jb = job_of(a, j);
     const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     const int64_t q0 = g * N;
+    if (N <= 64 && et == 0) *c.bw_job = (int)j;
     if (et < N) {
       const bool real = q0 + et < a.nq;
       float cmabs = 0.0f;
@@ -544,6 +594,10 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
           if (!ip) sc = c.qnorm_s[n] + cur.nrm - 2.0f * sc;
           const uint64_t key = make_key(sc, (uint32_t)rw, st.metric);
           if (key < c.thr[n]) mybuf[n * a.cap + atomicAdd(reinterpret_cast<int*>(&c.fq[n].w), 1)] = key;
+          if (N <= 64 && a.best_j && q0 + n < a.nq)
+            atomicMin(reinterpret_cast<unsigned long long*>(a.seg_best) +
+                          ((q0 + n) * a.segs + jb.s) * a.best_j + (int)(rw % a.best_j),
+                      (unsigned long long)key);
         }
       }
       tc_fence_before();
@@ -605,13 +659,38 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
     named_bar(1, kEpiThreads);
   }
 out:
+  if (N <= 64 && et == 0) *c.bw_job = -2;
   return;
+}
+
+// The bound warp: while the epilogue works on a job, it takes the job's
+// queries in turn and lowers each one's shared bound to the union bound of
+// the lowest keys every segment has found so far (union_bound).  It waits on
+// nothing: it reads the epilogue's job index, and stops when the epilogue
+// marks its exit (or after a pass limit).
+template <int N>
+__device__ __forceinline__ void bound_role(const MmaArgs& a, const Ctx& c, int lane) {
+  if (!a.best_j) return;
+  const int P = a.segs * a.best_j;
+  for (uint32_t pass = 0; pass < (1u << 24); ++pass) {
+    const int jv = __shfl_sync(kFull, *c.bw_job, 0);
+    if (jv == -2) return;
+    if (jv < 0) {
+      __nanosleep(256);
+      continue;
+    }
+    const int64_t q0 = job_of(a, jv).g * N;
+    for (int n = 0; n < N && q0 + n < a.nq; ++n) {
+      const uint64_t b = union_bound(a.seg_best + (q0 + n) * P, P, a.k1, lane);
+      if (lane == 0 && b != kNoKey) atomicMin(reinterpret_cast<unsigned long long*>(a.gthr + q0 + n), b);
+    }
+  }
 }
 
 #undef LVQ_WAIT
 
 template <int N, int BITS, int CM>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(warps_of<N>() * 32, 1)
     scan_mma_kernel(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap qmap, MmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
@@ -631,6 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.cm16 = reinterpret_cast<__half*>(c.hist + 4 * kHistInts);  // used when CM == 1
   c.cm32 = reinterpret_cast<float*>(c.hist + 4 * kHistInts);   // used when CM == 2
   c.ep_go = reinterpret_cast<volatile int*>(smem + L.misc + 20);  // two ints
+  c.bw_job = reinterpret_cast<volatile int*>(smem + L.misc + 28);
   c.B = bars_at(bar_mem);
   c.grid = gridDim.x;
   c.cta = blockIdx.x;
@@ -653,6 +733,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(c.B.q_empty, 1);
     mbar_init(c.B.mma_done, 1);
     *c.abort_sh = 0;
+    *c.bw_job = -1;
     fence_mbar_init();
   }
   if (warp == 1) tmem_alloc(tmem_base_sh, kTmemCols);
@@ -671,8 +752,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) mma_role<N, BITS>(a, c);
   } else if (warp < kEpiWarp0) {
     unpack_role<N, BITS>(a, c, warp, lane);
-  } else {
+  } else if (warp < kBoundWarp) {
     epilogue_role<N, BITS, CM>(a, c, warp, lane);
+  } else if (N <= 64) {
+    bound_role<N>(a, c, lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -721,7 +804,7 @@ cudaError_t launch_nbc(const CUtensorMap& cm, const CUtensorMap& qm, const MmaAr
   static std::atomic<uint64_t> attr{0};
   const cudaError_t e = max_dyn_smem_once((const void*)scan_mma_kernel<N, BITS, CM>, 232448, attr);
   if (e != cudaSuccess) return e;
-  scan_mma_kernel<N, BITS, CM><<<grid, kThreads, smem, stream>>>(cm, qm, a);
+  scan_mma_kernel<N, BITS, CM><<<grid, warps_of<N>() * 32, smem, stream>>>(cm, qm, a);
   return cudaGetLastError();
 }
 
@@ -807,6 +890,8 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   a.counts = plan.counts;
   a.gthr = plan.gthr;
   a.wait_limit = plan.wait_polls > 0 ? plan.wait_polls : kWaitLimit;
+  a.seg_best = plan.seg_best;
+  a.best_j = plan.seg_best ? plan.best_j : 0;
   if (!a.counts || !a.gthr || a.segs < 1 || a.segs > a.ntiles) return cudaErrorInvalidValue;
   const int grid = plan.grid;
 
@@ -827,6 +912,10 @@ cudaError_t launch_scan_mma(const DeviceStore& st, int64_t nq, const QueryPrep& 
   }
   cudaError_t e = cudaMemsetAsync(plan.gthr, 0xFF, (size_t)nq * 8, stream);
   if (e != cudaSuccess) return e;
+  if (a.best_j) {
+    e = cudaMemsetAsync(a.seg_best, 0xFF, (size_t)nq * a.segs * a.best_j * 8, stream);
+    if (e != cudaSuccess) return e;
+  }
   // as many code stages as shared memory allows (more bytes in flight for
   // narrow query tiles)
   // The table of <q, mu_m> is held in float32 when it fits beside three
