@@ -367,20 +367,6 @@ __device__ __forceinline__ int g_dp4a_us(uint32_t a, uint32_t b, int c) {
   asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
-// Read-only loads of a record's words that ask L2 to fetch only the 64-byte
-// half line the word is in: a randomly addressed 64-byte record then costs 64
-// bytes of DRAM traffic, not a whole 128-byte line.
-__device__ __forceinline__ uint32_t ldg_half_line(const uint32_t* p) {
-  uint32_t v;
-  asm("ld.global.nc.L2::64B.u32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ uint2 ldg_half_line(const uint2* p) {
-  uint2 v;
-  asm("ld.global.nc.L2::64B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-  return v;
-}
-
 // Dim (within its group of 8) of byte b of the query word that meets code
 // bytes in dp4a: for 4-bit codes half h = 0 pairs with (w & 0x0F0F0F0F),
 // dims (0, 4, 1, 5), h = 1 with ((w >> 4) & 0x0F0F0F0F), dims (2, 6, 3, 7);
@@ -682,25 +668,22 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
   cp_async_wait<0>();
 }
 
-// ---- ID-gather search with the query in registers (d <= 768) -----------------
-// One query at a time per 128-thread block (persistent blocks).  A row is
-// scored by L consecutive lanes (a power of two); lane l owns the 8-dim code
-// groups l, l + L, .., at most three, and holds the query's four byte planes
-// for those groups in registers for the whole query, so a row costs its code
-// words (read straight from HBM into registers, lanes of a row reading
-// consecutive words) and dp4a, with no shared-memory traffic for the query.
-// Each record's 16-byte trailer (l, D, ||x^||^2, mean id) comes with it, so
-// a candidate is one record read (lane l of a row loads trailer word l, so a
-// row's four lanes hold it in one register each).  Each warp keeps P steps of
-// R = 32 / L rows in flight (loads for step t + P issued as step t is
-// scored).  The exact
-// integer products and the score follow the fixed-point scheme above.
+// ---- ID-gather search with the query in registers (short records) ----------
+// One query at a time per 128-thread block (persistent blocks).  A record
+// (code words, then the 16-byte trailer l, D, ||x^||^2, mean id) is read by
+// L consecutive lanes (a power of two), lane l loading its 16-byte chunk l in
+// one access, so a candidate costs one load instruction per lane; lanes
+// below row1 / 16 hold four code words each (4-bit: four 8-dim groups,
+// 8-bit: two), the lane of chunk row1 / 16 holds the trailer.  Each lane
+// keeps the query's four byte planes for its code words in registers for the
+// whole query, so a row costs its record read and dp4a, with no shared-memory
+// traffic for the query.  Each warp keeps P steps of R = 32 / L rows in
+// flight (the loads of step t + P are issued as step t is scored; the
+// candidate ids a round earlier still).  The exact integer products and the
+// score follow the fixed-point scheme above; the trailer's lane scores the row.
 constexpr int kG2Threads = 128;
 constexpr int kG2Warps = kG2Threads / 32;
-#ifndef LVQ_G2_STEPS
-#define LVQ_G2_STEPS 4
-#endif
-constexpr int kG2Steps = LVQ_G2_STEPS;  // steps of R rows each warp keeps in flight
+constexpr int kG2Steps = 4;  // steps of R rows each warp keeps in flight
 
 __host__ __device__ inline int pow2_ceil(int v) {
   int p = 1;
@@ -708,12 +691,24 @@ __host__ __device__ inline int pow2_ceil(int v) {
   return p;
 }
 
-template <int GL, int BITS, int L>
+// One 16-byte chunk of a record, asking L2 for its 64-byte half line only:
+// a randomly addressed 64-byte record then costs 64 bytes of DRAM traffic,
+// not a whole 128-byte line.
+__device__ __forceinline__ uint4 ldg_chunk(const void* p) {
+  uint4 v;
+  asm("ld.global.nc.L2::64B.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
+template <int BITS, int L>
 __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, const float* __restrict__ q, int64_t nq,
                                                              QueryPrep p, const int64_t* __restrict__ cand, int n_cand,
                                                              int k, int cap, int64_t* out_ids, float* out_scores) {
   constexpr int P = kG2Steps;
-  constexpr int WPG = BITS == 4 ? 1 : 2;  // code words per 8-dim group
+  constexpr int GPC = BITS == 4 ? 4 : 2;  // 8-dim code groups per 16-byte chunk
+  constexpr int R = 32 / L;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* buf = reinterpret_cast<uint64_t*>(smem);  // [cap]
   int* sh_pos = reinterpret_cast<int*>(buf + cap);    // [k + 2]
@@ -723,9 +718,11 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
   __shared__ float qmax_sh[kG2Warps];
   __shared__ long long qsum_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int d = st.d, W = (d + 7) >> 3;
-  constexpr int R = 32 / L;
+  const int d = st.d, W = (d + 7) >> 3;  // 8-dim groups
   const int r = lane / L, l = lane % L;
+  const int tchunk = st.row1 >> 4;       // the trailer's chunk
+  const bool has_chunk = 16 * l < st.stride1;
+  const bool scorer = l == tchunk;
   const bool ip = st.metric == LVQ_IP;
   const long long ioff = BITS == 4 ? 8 : 128;
   const float off = BITS == 4 ? 8.0f : 128.0f;
@@ -748,19 +745,21 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
     for (int i = 0; i < kG2Warps; ++i) mx = fmaxf(mx, qmax_sh[i]);
     const int qe = mx > 0.0f ? ilogbf(mx) - 30 : 0;
     const float qscale = mx > 0.0f ? ldexpf(1.0f, qe) : 0.0f;
-    // this lane's planes: pw[i][plane][half] for group l + L i
-    uint32_t pw[GL][4][2];
+    // this lane's planes: pw[i][plane][half] for group GPC l + i (none past
+    // the code chunks)
+    uint32_t pw[GPC][4][2];
     long long part = 0;
 #pragma unroll
-    for (int i = 0; i < GL; ++i) {
-      const int g = l + L * i;
+    for (int i = 0; i < GPC; ++i) {
+      const int g = GPC * l + i;
+      const bool mine = l < tchunk && g < W;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         pw[i][0][h] = pw[i][1][h] = pw[i][2][h] = pw[i][3][h] = 0u;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int j = 8 * g + plane_dim(BITS, h, b);
-          const int v = (g < W && j < d) ? max(-2147483647, __float2int_rn(ldexpf(qrow[j], -qe))) : 0;
+          const int v = (mine && j < d) ? max(-2147483647, __float2int_rn(ldexpf(qrow[j], -qe))) : 0;
           part += v;
           pw[i][0][h] |= (uint32_t)(v & 255) << (8 * b);
           pw[i][1][h] |= (uint32_t)((v >> 8) & 255) << (8 * b);
@@ -783,9 +782,8 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
     const float qn = ip ? 0.0f : p.qnorm[qi];
     const float* cmq = p.cm + qi * st.n_means;
     // the candidate rows of this warp's step t: s = kG2Warps t + warp, rows s R + r
-    uint32_t cw[P][GL * WPG];
-    uint32_t tw[P];  // trailer word l of the row
-    uint32_t lv[P];
+    uint4 ch[P];     // this lane's chunk of the row in flight
+    uint32_t lv[P];  // its live word (trailer lane)
     int sid[P];      // slot of the row whose record is in flight
     int nid[P];      // slot of the row one round later (its id read a round ahead)
     // a step's candidate id (-1: skipped); ids are read a round before the
@@ -799,45 +797,35 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
       }
       return id;
     };
-    auto load_rec = [&](int id, uint32_t(&cwu)[GL * WPG], uint32_t& twu, uint32_t& lvu) {
-      const uint8_t* rec = st.codes1 + (int64_t)(id < 0 ? 0 : id) * st.stride1;
-#pragma unroll
-      for (int gi = 0; gi < GL; ++gi) {
-        const int g = l + L * gi;
-        const bool in = id >= 0 && g < W;
-        if (BITS == 4) {
-          cwu[gi] = in ? ldg_half_line(reinterpret_cast<const uint32_t*>(rec) + g) : 0u;
-        } else {
-          const uint2 v = in ? ldg_half_line(reinterpret_cast<const uint2*>(rec) + g) : make_uint2(0u, 0u);
-          cwu[2 * gi] = v.x;
-          cwu[2 * gi + 1] = v.y;
-        }
-      }
-      twu = (l < 4 && id >= 0) ? ldg_half_line(reinterpret_cast<const uint32_t*>(rec + st.row1) + l) : 0u;
-      lvu = (l == 0 && id >= 0) ? __ldg(st.live + (id >> 5)) : 0u;
+    auto load_rec = [&](int id, uint4& chu, uint32_t& lvu) {
+      const unsigned char* rec = st.codes1 + (int64_t)(id < 0 ? 0 : id) * st.stride1;
+      chu = (id >= 0 && has_chunk) ? ldg_chunk(rec + 16 * l) : make_uint4(0u, 0u, 0u, 0u);
+      lvu = (id >= 0 && scorer) ? __ldg(st.live + (id >> 5)) : 0u;
     };
 #pragma unroll
     for (int u = 0; u < P; ++u) sid[u] = load_id(u);
 #pragma unroll
     for (int u = 0; u < P; ++u) {
-      load_rec(sid[u], cw[u], tw[u], lv[u]);
+      load_rec(sid[u], ch[u], lv[u]);
       nid[u] = load_id(P + u);
     }
     for (int rd = 0; rd < rounds; ++rd) {
 #pragma unroll
       for (int u = 0; u < P; ++u) {
         GatherAcc A = {0u, 0u, 0u, 0};
+        const uint32_t cw[4] = {ch[u].x, ch[u].y, ch[u].z, ch[u].w};
 #pragma unroll
-        for (int gi = 0; gi < GL; ++gi) {
-          const uint32_t x0 = BITS == 4 ? (cw[u][gi] & 0x0F0F0F0Fu) : cw[u][WPG * gi];
-          const uint32_t x1 = BITS == 4 ? ((cw[u][gi] >> 4) & 0x0F0F0F0Fu) : cw[u][WPG * gi + WPG - 1];
-          plane_step(A, x0, x1, make_uint2(pw[gi][0][0], pw[gi][0][1]), make_uint2(pw[gi][1][0], pw[gi][1][1]),
-                     make_uint2(pw[gi][2][0], pw[gi][2][1]), make_uint2(pw[gi][3][0], pw[gi][3][1]));
+        for (int i = 0; i < GPC; ++i) {
+          const uint32_t x0 = BITS == 4 ? (cw[i] & 0x0F0F0F0Fu) : cw[2 * i];
+          const uint32_t x1 = BITS == 4 ? ((cw[i] >> 4) & 0x0F0F0F0Fu) : cw[2 * i + 1];
+          plane_step(A, x0, x1, make_uint2(pw[i][0][0], pw[i][0][1]), make_uint2(pw[i][1][0], pw[i][1][1]),
+                     make_uint2(pw[i][2][0], pw[i][2][1]), make_uint2(pw[i][3][0], pw[i][3][1]));
         }
         // planes 0 + 1 and 2 + 3 in 32 bits each, exactly: with c <= 2^B1 - 1
-        // and d <= 192 (at most 24 groups of 8 dims), the first pair is at
-        // most d (2^B1 - 1) 255 257 < 2^32 (unsigned) and the second (plane 3
-        // signed) at most d (2^B1 - 1) (255 + 128 256) < 2^31 in magnitude
+        // and at most 28 groups of 8 dims (224 dims, 4-bit) or 14 (112,
+        // 8-bit), the first pair is at most 8 W (2^B1 - 1) 255 257 < 2^32
+        // (unsigned) and the second (plane 3 signed) at most
+        // 8 W (2^B1 - 1) (255 + 128 256) < 2^31 in magnitude
         uint32_t lo = A.a0 + (A.a1 << 8);
         int hi = (int)A.a2 + (A.a3 << 8);
 #pragma unroll
@@ -846,21 +834,19 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
           hi += __shfl_xor_sync(kFull, hi, o);
         }
         const long long dot = (long long)lo + ((long long)hi << 16);
-        const int rb = lane - l;  // the row's first lane
-        const uint4 t4 = make_uint4(__shfl_sync(kFull, tw[u], rb), __shfl_sync(kFull, tw[u], rb + 1),
-                                    __shfl_sync(kFull, tw[u], rb + 2), __shfl_sync(kFull, tw[u], rb + 3));
+        const uint4 t4 = ch[u];  // the trailer, in the scoring lane
         const int id = sid[u];
-        const bool live = id >= 0 && ((lv[u] >> (id & 31)) & 1u);
+        const bool live = scorer && id >= 0 && ((lv[u] >> (id & 31)) & 1u);
         // refill this slot with step t + P (its id is already here) while the
         // row is scored, and read the id of step t + 2 P
         sid[u] = nid[u];
-        load_rec(sid[u], cw[u], tw[u], lv[u]);
+        load_rec(sid[u], ch[u], lv[u]);
         nid[u] = load_id((rd + 2) * P + u);
-        if (l == 0 && live) {
-          const float lo = __uint_as_float(t4.x), stp = __uint_as_float(t4.y), nrm = __uint_as_float(t4.z);
+        if (live) {
+          const float lo_r = __uint_as_float(t4.x), stp = __uint_as_float(t4.y), nrm = __uint_as_float(t4.z);
           const int m = (int)t4.w;
           const float a = __fmul_rn(qscale, (float)(dot - qoff));
-          float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo), qs, cmq[m]));
+          float sc = __fmaf_rn(stp, a, __fmaf_rn(__fmaf_rn(off, stp, lo_r), qs, cmq[m]));
           if (!ip) sc = __fadd_rn(__fadd_rn(qn, nrm), -2.0f * sc);
           const uint64_t key = make_key(sc, (uint32_t)id, st.metric);
           if (key < thr) buf[atomicAdd(&cnt, 1)] = key;
@@ -977,30 +963,16 @@ GatherGeom gather_geom(int row1, int d, int k) {
   return g;  // does not fit: the launcher refuses it
 }
 
-// Lanes per row and groups per lane of gather2_kernel: the fewest lane slots
-// (L a power of two, at most three groups a lane), ties to more groups a
-// lane (fewer shuffles); {0, 0} when a row would need more than 8 lanes or
-// fewer than 4 (the four trailer words are spread over a row's lanes).
-// Measured on B300: at d = 96 (L = 4, eight rows a warp step) it beats the
-// shared-memory ring kernel (0.83 vs 1.16 ms for 8,192 x 2,048 ids); at
-// d = 768 (L = 32, one row a step) the per-row shuffles and loads cost more
-// than the ring kernel's plane reads (0.74 vs 0.43 ms for 1,024 x 2,048).
-static void gather2_shape(int d, int* L, int* GL) {
-  const int W = (d + 7) / 8;
-  *L = 0;
-  *GL = 0;
-  int best = 1 << 30;
-  for (int gl = 3; gl >= 1; --gl) {
-    const int l = pow2_ceil((W + gl - 1) / gl);
-    if (l >= 4 && l <= 8 && l * gl < best) {
-      best = l * gl;
-      *L = l;
-      *GL = gl;
-    }
-  }
+// Lanes per row of gather2_kernel: the record's 16-byte chunks rounded up to
+// a power of two, 2 to 8 (records of up to 128 bytes: d <= 224 at 4 bits,
+// d <= 112 at 8); 0 when the record is longer (the ring kernel takes it).
+static int gather2_lanes(const DeviceStore& st) {
+  if (st.bits1 != 4 && st.bits1 != 8) return 0;
+  const int l = pow2_ceil((int)(st.stride1 / 16));
+  return l >= 2 && l <= 8 ? l : 0;
 }
 
-template <int GL, int BITS, int L>
+template <int BITS, int L>
 static cudaError_t launch_gather2_t(const DeviceStore& st, const float* q, int64_t nq, const QueryPrep& p,
                                     const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
                                     cudaStream_t stream) {
@@ -1009,17 +981,17 @@ static cudaError_t launch_gather2_t(const DeviceStore& st, const float* q, int64
   const size_t smem = (size_t)cap * 8 + (size_t)(k + 2) * 4 + 16;
   static std::atomic<uint64_t> attr{0};
   {
-    const cudaError_t e = max_dyn_smem_once((const void*)gather2_kernel<GL, BITS, L>, 200 * 1024, attr);
+    const cudaError_t e = max_dyn_smem_once((const void*)gather2_kernel<BITS, L>, 200 * 1024, attr);
     if (e != cudaSuccess) return e;
   }
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather2_kernel<GL, BITS, L>, kG2Threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather2_kernel<BITS, L>, kG2Threads, smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t grid = std::min<int64_t>(nq, (int64_t)sms * per_sm);
-  gather2_kernel<GL, BITS, L><<<(unsigned)grid, kG2Threads, smem, stream>>>(st, q, nq, p, cand, n_cand, k, cap,
-                                                                              out_ids, out_scores);
+  gather2_kernel<BITS, L><<<(unsigned)grid, kG2Threads, smem, stream>>>(st, q, nq, p, cand, n_cand, k, cap, out_ids,
+                                                                          out_scores);
   return cudaGetLastError();
 }
 
@@ -1027,24 +999,14 @@ cudaError_t launch_gather(const DeviceStore& st, const float* q, int64_t nq, con
                           const int64_t* cand, int n_cand, int k, int64_t* out_ids, float* out_scores,
                           cudaStream_t stream) {
   if (nq <= 0) return cudaSuccess;
-  int L = 0, GL = 0;
-  gather2_shape(st.d, &L, &GL);
-  if (GL > 0 && (st.bits1 == 4 || st.bits1 == 8)) {
-    const int sel = (GL - 1) * 4 + (st.bits1 == 4 ? 0 : 2) + (L == 4 ? 0 : 1);
-#define LVQ_G2(gl, b, l) launch_gather2_t<gl, b, l>(st, q, nq, p, cand, n_cand, k, out_ids, out_scores, stream)
-    switch (sel) {
-      case 0: return LVQ_G2(1, 4, 4);
-      case 1: return LVQ_G2(1, 4, 8);
-      case 2: return LVQ_G2(1, 8, 4);
-      case 3: return LVQ_G2(1, 8, 8);
-      case 4: return LVQ_G2(2, 4, 4);
-      case 5: return LVQ_G2(2, 4, 8);
-      case 6: return LVQ_G2(2, 8, 4);
-      case 7: return LVQ_G2(2, 8, 8);
-      case 8: return LVQ_G2(3, 4, 4);
-      case 9: return LVQ_G2(3, 4, 8);
-      case 10: return LVQ_G2(3, 8, 4);
-      default: return LVQ_G2(3, 8, 8);
+  const int L = gather2_lanes(st);
+  if (L > 0) {
+    const bool b4 = st.bits1 == 4;
+#define LVQ_G2(b, l) launch_gather2_t<b, l>(st, q, nq, p, cand, n_cand, k, out_ids, out_scores, stream)
+    switch (L) {
+      case 2: return b4 ? LVQ_G2(4, 2) : LVQ_G2(8, 2);
+      case 4: return b4 ? LVQ_G2(4, 4) : LVQ_G2(8, 4);
+      default: return b4 ? LVQ_G2(4, 8) : LVQ_G2(8, 8);
     }
 #undef LVQ_G2
   }
