@@ -656,8 +656,11 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_kernel(DeviceStore s
       }
     }
     {
+      // the last cut sorts only the keys there are (rounded up to a power of two)
+      const int n_left = cnt;
+      const int span = pow2_at_least(n_left > 32 ? n_left : 32);
       uint64_t t;
-      const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
+      const int kept = block_select_dedupe(buf, span < cap ? span : cap, n_left, k, scan_sh, &t);
       if (threadIdx.x == 0) cnt = kept;
       __syncthreads();
     }
@@ -868,8 +871,11 @@ __global__ void __launch_bounds__(kG2Threads) gather2_kernel(DeviceStore st, con
       }
     }
     {
+      // the last cut sorts only the keys there are (rounded up to a power of two)
+      const int n_left = cnt;
+      const int span = pow2_at_least(n_left > 32 ? n_left : 32);
       uint64_t t;
-      const int kept = block_select_dedupe(buf, cap, cnt, k, scan_sh, &t);
+      const int kept = block_select_dedupe(buf, span < cap ? span : cap, n_left, k, scan_sh, &t);
       if (threadIdx.x == 0) cnt = kept;
       __syncthreads();
     }
