@@ -45,11 +45,16 @@ METRIC = "LVQ-4x8 distances/s & QPS@recall10 at 10M x 768"
 UNIT = "distances/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one scan_mma launch over
 # 2M rows with the bench's 12,716-query mix (ncu --set full, B300)
-SCAN_MMA_DRAM_BYTES_2M = 1.934105e9 + 0.774121e9
+SCAN_MMA_DRAM_BYTES_2M = 2.006203e9 + 0.844191e9
 # DRAM bytes (read + write) of one ID-gather launch of 1,024 queries x 2,048
 # candidate ids, from an ncu capture of the same launch size at 2M rows (the
 # launch's traffic depends on the candidates, not on the rows)
-GATHER_DRAM_BYTES = 836.396e6 + 4.395e6
+GATHER_DRAM_BYTES = 1.066799e9 + 4.035e6
+# the same for the 5M x 96 ID-gather launch (8,192 queries x 2,048 ids)
+GATHER2_C4_DRAM_BYTES = 1.060874e9 + 8.091e6
+# first-level bytes of a database row at d = 768, 4 bits: codes, lower, step,
+# mean id (IP reads no norm) and its live bit
+ROW_BYTES = 384 + 4 + 4 + 4 + 1 / 8
 
 
 def parse():
@@ -375,18 +380,19 @@ def c4_leg(n=5_000_000, nq=8192, C=2048, k1=50, k=10):
     qd, cd = torch.from_numpy(qh).cuda(), torch.from_numpy(cand).cuda()
     st.reserve(nq, k1, C)
     ms, kern = _timed(st, lambda: st.search_candidates(qd, cd, k, k1), reps=5)
-    row1 = (((w["d"] * 4 + 7) // 8 + 31) // 32) * 32
-    per_cand = row1 + 4 + 4 + 1 + 4 + 8   # codes row, l, D, mean id, ||x^||^2 (L2), candidate id
+    row1 = ((w["d"] * 4 // 8) + 15) // 16 * 16
+    per_cand = row1 + 16 + 8   # the record (codes, then l, D, ||x^||^2, mean id) and the candidate id
     g_ms = kern.get("gather")
     peak = peaks_file().get("hbm_gbs")
     gbs = nq * C * per_cand / g_ms / 1e6 if g_ms else None
     st.close()
     return {"workload": name, "n": n, "d": w["d"], "metric": "l2", "queries": nq, "candidates": C, "k1": k1, "k": k,
             "search_ms": ms, "kernel_ms": kern, "qps": nq / (ms / 1e3),
-            "gather_roofline": {"kernel": "gather_kernel", "bound": "hbm", "bytes_per_candidate": per_cand,
+            "gather_roofline": {"kernel": "gather2_kernel", "bound": "hbm", "bytes_per_candidate": per_cand,
                                 "algorithmic_bytes_per_launch": nq * C * per_cand, "kernel_ms": g_ms,
                                 "achieved": gbs, "peak": peak, "unit": "GB/s",
                                 "frac": gbs / peak if gbs and peak else None,
+                                "traffic": GATHER2_C4_DRAM_BYTES if (n, nq, C) == (5_000_000, 8192, 2048) else None,
                                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else None}}
 
 
@@ -704,12 +710,12 @@ def main():
         e2e = {"value": u2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # small batches: the integer scan against the HBM roofline
-    bytes_per_row = 384 + 4 + 4 + 1  # 4-bit codes, lower, step, mean id (IP reads no norm)
+    bytes_per_row = ROW_BYTES
     hbm_peak = peaks_file().get("hbm_gbs")
     small = None
     if not args.no_small:
         small = []
-        for nqs in (1, 2, 4, 16, 64):
+        for nqs in (1, 2, 4, 8, 16, 32, 64):
             qs = q_dev[:nqs].contiguous()
             for _ in range(3):
                 st.search(qs, 10, 100, "auto")
@@ -749,7 +755,7 @@ def main():
     scan_ms, scan_launches = prof[scan_kind]
     peaks = peaks_file()
     flops_per_launch = 2.0 * nq * n_live * d
-    bytes_per_launch = n_live * (384 + 8 + 1)
+    bytes_per_launch = n_live * ROW_BYTES
     per_launch_s = scan_ms / 1e3 / max(scan_launches, 1)
     if scan_kind == "scan_mma":
         achieved = flops_per_launch / per_launch_s / 1e12
@@ -772,7 +778,7 @@ def main():
     # the ID-gather kernel of the step (candidate ids, codes and per-row
     # constants of every candidate, re-rank reads not counted)
     g_ms = prof["gather"][0] / max(prof["gather"][1], 1)
-    g_bytes = nq_g * C * (384 + 4 + 4 + 1 + 8)
+    g_bytes = nq_g * C * (384 + 16 + 8)  # the record (codes and trailer) and the candidate id
     gather_roof = {"kernel": "gather_kernel", "kernel_ms": g_ms, "algorithmic_bytes_per_launch": g_bytes,
                    "hbm_gbs": g_bytes / g_ms / 1e6 if g_ms else None, "peak_gbs": peaks.get("hbm_gbs"),
                    "frac": g_bytes / g_ms / 1e6 / peaks["hbm_gbs"] if g_ms and peaks.get("hbm_gbs") else None,
