@@ -709,6 +709,10 @@ def main():
         u2, t2 = aggregate(dist_per_step * args.steps, t_e2e, world)
         e2e = {"value": u2 / t2, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # the autotuned tile width was for the step's 12,716-query batch; the
+    # other legs on this store pick their tiles by batch size
+    if tuning:
+        st.set_tuning()
     # small batches: the integer scan against the HBM roofline
     bytes_per_row = ROW_BYTES
     hbm_peak = peaks_file().get("hbm_gbs")
