@@ -108,19 +108,25 @@ struct MmaArgs {
 
 struct Smem {
   // offsets from the 1024-aligned base
-  int q, code, bars, misc;
+  int q, code, bars, misc, cm;
   int total;
 };
 
+// The small per-CTA state comes first, at offsets that depend on n only,
+// so that the epilogue reaches it from the base with constant offsets
+// (fewer registers held across its loop); the query tile (1024-byte
+// aligned for its swizzle) and the code stages follow.
+//   misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 +
+//         qnorm[n] + cmabs[n] + hist[4][kHistInts]; then the mbarriers
+//         (64 x 8 B) and <q, mu_m> of the tile (cm_bytes, when held)
 __host__ __device__ inline Smem smem_layout(int n, int qboxes, int stages, int cm_bytes) {
   Smem s;
-  s.q = 0;
-  s.code = qboxes * n * 128;
-  s.bars = s.code + stages * kStageBytes;
-  s.misc = s.bars + 64 * 8;
-  // misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 + qnorm[n] + cmabs[n]
-  //       + hist[4][kHistInts] + cm16[n][M] (when held)
-  s.total = s.misc + 32 + n * 8 + n * 16 + n * 4 * 2 + 4 * kHistInts * 4 + cm_bytes;
+  s.misc = 0;
+  s.bars = 32 + n * 8 + n * 16 + n * 4 * 2 + 4 * kHistInts * 4;
+  s.cm = s.bars + 64 * 8;
+  s.q = (s.cm + cm_bytes + 1023) / 1024 * 1024;
+  s.code = s.q + qboxes * n * 128;
+  s.total = s.code + stages * kStageBytes;
   return s;
 }
 
@@ -707,8 +713,8 @@ __global__ void __launch_bounds__(warps_of<N>() * 32, 1)
   c.qnorm_s = reinterpret_cast<float*>(c.fq + N);
   c.cmabs_s = c.qnorm_s + N;
   c.hist = reinterpret_cast<int*>(c.cmabs_s + N);
-  c.cm16 = reinterpret_cast<__half*>(c.hist + 4 * kHistInts);  // used when CM == 1
-  c.cm32 = reinterpret_cast<float*>(c.hist + 4 * kHistInts);   // used when CM == 2
+  c.cm16 = reinterpret_cast<__half*>(smem + L.cm);  // used when CM == 1
+  c.cm32 = reinterpret_cast<float*>(smem + L.cm);   // used when CM == 2
   c.ep_go = reinterpret_cast<volatile int*>(smem + L.misc + 20);  // two ints
   c.bw_job = reinterpret_cast<volatile int*>(smem + L.misc + 28);
   c.B = bars_at(bar_mem);
