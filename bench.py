@@ -45,13 +45,13 @@ METRIC = "LVQ-4x8 distances/s & QPS@recall10 at 10M x 768"
 UNIT = "distances/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one scan_mma launch over
 # 2M rows with the bench's 12,716-query mix (ncu --set full, B300)
-SCAN_MMA_DRAM_BYTES_2M = 2.006203e9 + 0.844191e9
+SCAN_MMA_DRAM_BYTES_2M = 2.05227e9 + 0.827707e9
 # DRAM bytes (read + write) of one ID-gather launch of 1,024 queries x 2,048
 # candidate ids, from an ncu capture of the same launch size at 2M rows (the
 # launch's traffic depends on the candidates, not on the rows)
 GATHER_DRAM_BYTES = 1.066799e9 + 4.035e6
 # the same for the 5M x 96 ID-gather launch (8,192 queries x 2,048 ids)
-GATHER2_C4_DRAM_BYTES = 1.060874e9 + 8.091e6
+GATHER2_C4_DRAM_BYTES = 1.060708e9 + 8.123e6
 # first-level bytes of a database row at d = 768, 4 bits: codes, lower, step,
 # mean id (IP reads no norm) and its live bit
 ROW_BYTES = 384 + 4 + 4 + 4 + 1 / 8
