@@ -468,9 +468,9 @@ cudaError_t launch_qb(const CUtensorMap& cm, const SmallArgs& a, int grid, size_
 // rows keys), so k1 kept keys and one tile of new ones always fit
 int small_cap(int k1, int rpt) { return pow2_at_least(k1 + kRows * rpt); }
 int small_wp(const DeviceStore& st) { return (int)ceil_div(st.row1, kBoxBytes) * (kBoxBytes / 4); }
-int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : 4; }
+int small_qb(int64_t nq) { return nq <= 1 ? 1 : nq <= 2 ? 2 : nq <= 3 ? 3 : 4; }
 // consumer groups: more warps hide more load latency, while the registers of
-// more queries allow fewer of them (4, 3 and 2 groups for 1, 2 and 4 slots)
+// more queries allow fewer of them (4, 3 and 2 groups for 1, 2 and 3-4 slots)
 int small_groups(int qb, int rpt) { return qb <= 1 ? 4 : qb <= 2 ? 3 : 2; }
 
 // ring stages per ring: as many as shared memory holds, up to kMaxRingStages;
@@ -562,6 +562,10 @@ cudaError_t launch_scan_small(const DeviceStore& st, int64_t nq, const QueryPrep
       if (rpt == 2)
         return b4 ? launch_qb<2, 4, 3, 2>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3, 2>(cm, a, grid, smem, stream);
       return b4 ? launch_qb<2, 4, 3, 1>(cm, a, grid, smem, stream) : launch_qb<2, 8, 3, 1>(cm, a, grid, smem, stream);
+    case 3:
+      if (rpt == 2)
+        return b4 ? launch_qb<3, 4, 2, 2>(cm, a, grid, smem, stream) : launch_qb<3, 8, 2, 2>(cm, a, grid, smem, stream);
+      return b4 ? launch_qb<3, 4, 2, 1>(cm, a, grid, smem, stream) : launch_qb<3, 8, 2, 1>(cm, a, grid, smem, stream);
     default:
       if (rpt == 2)
         return b4 ? launch_qb<4, 4, 2, 2>(cm, a, grid, smem, stream) : launch_qb<4, 8, 2, 2>(cm, a, grid, smem, stream);
