@@ -25,7 +25,7 @@
 //               ring in TMEM;
 //   warps 10-17 epilogue (two per TMEM lane quarter, each taking half of the
 //               query columns): tcgen05.ld of the float32 accumulators
-//               (double buffered in TMEM) 16 columns at a time, a cheap
+//               (double buffered in TMEM) 8 to 32 columns at a time, a cheap
 //               per-query filter, then the exact key and the top-k1
 //               threshold test for the few rows that pass it;
 //   warp 18     (query tiles of up to 64) bound: lowers each query's
@@ -272,8 +272,14 @@ out:
   if (qi > 0) mbar_wait(c.B.q_full, (qi - 1) & 1, kWaitLimit);
 }
 
+// Run by the whole warp 1: every lane waits on the mbarriers and one elected
+// lane (elect.sync) issues the MMAs and commits.  Measured on B300, a
+// converged warp issues back-to-back M = 128, K = 16 MMAs at the full rate
+// (64 cycles each at N = 128) with a wait and a commit every 8 of them,
+// where a lone thread in a divergent branch took 90 cycles per MMA (and 59
+// at N <= 64 even without waits, against 19 from a converged warp).
 template <int N, int BITS>
-__device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
+__device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c, int lane) {
   constexpr int kBoxDims = BITS == 4 ? 128 : 64;
   constexpr int kACols = kBoxDims / 2;
   constexpr int kKSteps = kBoxDims / 16;
@@ -283,45 +289,63 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c) {
   RingPos ap;  // A ring position
   int64_t g_cur = -1;
   const uint32_t qbase = smem_u32(c.qs);
-  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+  // a bounded wait whose verdict the whole warp shares
+#define LVQ_WAIT_WARP(bar, par)                                        \
+  do {                                                                 \
+    if (!__all_sync(kFull, mbar_wait((bar), (par), a.wait_limit))) {   \
+      if (lane == 0) {                                                 \
+        *c.abort_sh = 1;                                               \
+        set_error(a.st.err, LVQ_ETIMEOUT);                             \
+      }                                                                \
+      goto out;                                                        \
+    }                                                                  \
+  } while (0)
+  for (int64_t j = c.cta; j < a.jobs && !__any_sync(kFull, *c.abort_sh); j += c.grid) {
     const Job jb = job_of(a, j);
     const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     if (g != g_cur) {
-      LVQ_WAIT(c, c.B.q_full, qi & 1);
+      LVQ_WAIT_WARP(c.B.q_full, qi & 1);
       ++qi;
       g_cur = g;
       tc_fence_after();
     }
     for (int64_t t = t0; t < t1; ++t) {
       const int db = di & 1;
-      LVQ_WAIT(c, c.B.d_empty + db, ((di >> 1) & 1) ^ 1);
+      LVQ_WAIT_WARP(c.B.d_empty + db, ((di >> 1) & 1) ^ 1);
       tc_fence_after();
       const uint32_t d_tmem = c.tbase + db * N;
       for (int kb = 0; kb < a.n_kbox; ++kb) {
         const int s = ap.stage;
-        LVQ_WAIT(c, c.B.a_full + s, ap.phase);
+        LVQ_WAIT_WARP(c.B.a_full + s, ap.phase);
         tc_fence_after();
         const uint32_t a_tmem = c.tbase + 2 * N + s * kACols;
         // K step kk of this box reads query dims kg .. kg+15, kg = kb*box + 16kk:
         // 64-dim query box kg/64 (N x 128 bytes each), byte offset 2*(kg%64)
         const uint64_t d0 = desc_sw128(qbase + (uint32_t)(kb * kBoxDims / 64) * N * 128);
+        if (elect_one()) {
 #pragma unroll
-        for (int kk = 0; kk < kKSteps; ++kk) {
-          const uint32_t off16 = (uint32_t)((kk * 16 / 64) * N * 128 + ((kk * 16) % 64) * 2) >> 4;
-          mma_f16_ts(d_tmem, a_tmem + kk * 8, d0 + off16, kIdesc, (kb | kk) != 0);
+          for (int kk = 0; kk < kKSteps; ++kk) {
+            const uint32_t off16 = (uint32_t)((kk * 16 / 64) * N * 128 + ((kk * 16) % 64) * 2) >> 4;
+            mma_f16_ts(d_tmem, a_tmem + kk * 8, d0 + off16, kIdesc, (kb | kk) != 0);
+          }
+          mma_commit(c.B.a_empty + s);
         }
-        mma_commit(c.B.a_empty + s);
+        __syncwarp();
         ap.advance(1, AS);
       }
-      mma_commit(c.B.d_full + db);
+      if (elect_one()) mma_commit(c.B.d_full + db);
+      __syncwarp();
       ++di;
     }
-    mma_commit(c.B.q_empty);
+    if (elect_one()) mma_commit(c.B.q_empty);
+    __syncwarp();
   }
 out:
-  // all MMAs issued by this thread are complete before TMEM is freed
-  mma_commit(c.B.mma_done);
-  mbar_wait(c.B.mma_done, 0, kWaitLimit);
+  // all MMAs issued by this warp are complete before TMEM is freed
+  if (elect_one()) mma_commit(c.B.mma_done);
+  __syncwarp();
+  (void)__all_sync(kFull, mbar_wait(c.B.mma_done, 0, kWaitLimit));
+#undef LVQ_WAIT_WARP
 }
 
 template <int N, int BITS>
@@ -467,9 +491,8 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
   const int ew = warp - kEpiWarp0;  // 0..7
   const int et = ew * 32 + lane;    // 0..255
   const int row_in = quarter * 32 + lane;
-  // columns of this warp: warps 0-3 the first half, 4-7 the second (all
-  // sixteen columns to the first set when N = 16)
-  constexpr int kHalf = N >= 32 ? N / 2 : N;
+  // columns of this warp: warps 0-3 the first half, 4-7 the second
+  constexpr int kHalf = N / 2;
   const int col0 = (ew >> 2) * kHalf;
   const int col1 = col0 + kHalf <= N ? col0 + kHalf : N;
   const uint32_t lane_base = c.tbase + ((uint32_t)(quarter * 32) << 16);
@@ -560,7 +583,9 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
 #pragma unroll
       for (int part = 0; part < kHalf / kPart; ++part) {
         uint32_t v[kPart];
-        if constexpr (kPart == 16) {
+        if constexpr (kPart == 8) {
+          tmem_ld_x8<0>(lane_base + db * N + col0, v);
+        } else if constexpr (kPart == 16) {
           tmem_ld_x16<0>(lane_base + db * N + col0, v);
         } else {
           tmem_ld_x32<0>(lane_base + db * N + col0 + part * 32, v);
@@ -755,7 +780,7 @@ __global__ void __launch_bounds__(warps_of<N>() * 32, 1)
   if (warp == 0) {
     if (lane == 0) producer_role<N, BITS>(&cmap, &qmap, a, c);
   } else if (warp == 1) {
-    if (lane == 0) mma_role<N, BITS>(a, c);
+    mma_role<N, BITS>(a, c, lane);
   } else if (warp < kEpiWarp0) {
     unpack_role<N, BITS>(a, c, warp, lane);
   } else if (warp < kBoundWarp) {
