@@ -80,6 +80,7 @@ constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
 constexpr int kHistInts = 64;           // 6-bit-digit radix histogram of one warp
+constexpr int kMetaAhead = 4;           // tiles between the L2 prefetch of row constants and their use
 
 struct MmaArgs {
   DeviceStore st;
@@ -223,53 +224,64 @@ struct Ctx {
   int cta, grid;
 };
 
-// Bounded wait; on expiry record LVQ_ETIMEOUT, tell the other roles, and
-// jump to the role's exit (a label `out` in the calling function).
-#define LVQ_WAIT(c, bar, par)                            \
-  do {                                                   \
-    if (!mbar_wait((bar), (par), a.wait_limit)) {        \
-      *(c).abort_sh = 1;                                 \
-      set_error(a.st.err, LVQ_ETIMEOUT);                 \
-      goto out;                                          \
-    }                                                    \
+// Bounded wait by a whole warp, whose lanes share the verdict; on expiry
+// record LVQ_ETIMEOUT, tell the other roles, and jump to the role's exit (a
+// label `out` in the calling function, which has `lane` and `a` in scope).
+#define LVQ_WAIT_WARP(c, bar, par)                                     \
+  do {                                                                 \
+    if (!__all_sync(kFull, mbar_wait((bar), (par), a.wait_limit))) {   \
+      if (lane == 0) {                                                 \
+        *(c).abort_sh = 1;                                             \
+        set_error(a.st.err, LVQ_ETIMEOUT);                             \
+      }                                                                \
+      goto out;                                                        \
+    }                                                                  \
   } while (0)
 
+// Run by the whole warp 0, like the MMA role: every lane waits, one elected
+// lane issues the copies.
 template <int N, int BITS>
 __device__ __forceinline__ void producer_role(const CUtensorMap* cmap, const CUtensorMap* qmap, const MmaArgs& a,
-                                              const Ctx& c) {
+                                              const Ctx& c, int lane) {
   uint32_t ci = 0, qi = 0;
   RingPos cp;  // code ring position of box ci
   int64_t g_cur = -1;
-  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+  for (int64_t j = c.cta; j < a.jobs && !__any_sync(kFull, *c.abort_sh); j += c.grid) {
     const Job jb = job_of(a, j);
     const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     if (g != g_cur) {
-      if (qi > 0) LVQ_WAIT(c, c.B.q_empty, (qi - 1) & 1);
-      mbar_expect_tx(c.B.q_full, (uint32_t)(a.qboxes * N * 128));
-      for (int kb = 0; kb < a.qboxes; ++kb)
-        tma_load_2d(c.qs + kb * N * 128, qmap, c.B.q_full, kb * 64, (int)(g * N));
+      if (qi > 0) LVQ_WAIT_WARP(c, c.B.q_empty, (qi - 1) & 1);
+      if (elect_one()) {
+        mbar_expect_tx(c.B.q_full, (uint32_t)(a.qboxes * N * 128));
+        for (int kb = 0; kb < a.qboxes; ++kb)
+          tma_load_2d(c.qs + kb * N * 128, qmap, c.B.q_full, kb * 64, (int)(g * N));
+      }
+      __syncwarp();
       ++qi;
       g_cur = g;
     }
     for (int64_t t = t0; t < t1; ++t) {
       for (int kb = 0; kb < a.n_kbox; ++kb) {
         const int s = cp.stage;
-        LVQ_WAIT(c, c.B.code_empty + s, cp.phase ^ 1);
-        mbar_expect_tx(c.B.code_full + s, kStageBytes);
-        tma_load_2d(c.cst + s * kStageBytes, cmap, c.B.code_full + s, kb * kBoxBytes, (int)(t * kRows));
+        LVQ_WAIT_WARP(c, c.B.code_empty + s, cp.phase ^ 1);
+        if (elect_one()) {
+          mbar_expect_tx(c.B.code_full + s, kStageBytes);
+          tma_load_2d(c.cst + s * kStageBytes, cmap, c.B.code_full + s, kb * kBoxBytes, (int)(t * kRows));
+        }
+        __syncwarp();
         ++ci;
         cp.advance(1, a.code_stages);
       }
     }
   }
 out:
-  // copies that may still be in flight: the last (up to) 3 code boxes and
-  // the last query tile
+  // copies that may still be in flight: the last (up to) code_stages code
+  // boxes and the last query tile
   for (uint32_t j = 1; j <= (uint32_t)a.code_stages && j <= ci; ++j) {
     const uint32_t k = ci - j;
-    mbar_wait(c.B.code_full + k % a.code_stages, (k / a.code_stages) & 1, kWaitLimit);
+    (void)__all_sync(kFull, mbar_wait(c.B.code_full + k % a.code_stages, (k / a.code_stages) & 1, kWaitLimit));
   }
-  if (qi > 0) mbar_wait(c.B.q_full, (qi - 1) & 1, kWaitLimit);
+  if (qi > 0) (void)__all_sync(kFull, mbar_wait(c.B.q_full, (qi - 1) & 1, kWaitLimit));
 }
 
 // Run by the whole warp 1: every lane waits on the mbarriers and one elected
@@ -290,33 +302,23 @@ __device__ __forceinline__ void mma_role(const MmaArgs& a, const Ctx& c, int lan
   int64_t g_cur = -1;
   const uint32_t qbase = smem_u32(c.qs);
   // a bounded wait whose verdict the whole warp shares
-#define LVQ_WAIT_WARP(bar, par)                                        \
-  do {                                                                 \
-    if (!__all_sync(kFull, mbar_wait((bar), (par), a.wait_limit))) {   \
-      if (lane == 0) {                                                 \
-        *c.abort_sh = 1;                                               \
-        set_error(a.st.err, LVQ_ETIMEOUT);                             \
-      }                                                                \
-      goto out;                                                        \
-    }                                                                  \
-  } while (0)
   for (int64_t j = c.cta; j < a.jobs && !__any_sync(kFull, *c.abort_sh); j += c.grid) {
     const Job jb = job_of(a, j);
     const int64_t g = jb.g, t0 = jb.t0, t1 = jb.t1;
     if (g != g_cur) {
-      LVQ_WAIT_WARP(c.B.q_full, qi & 1);
+      LVQ_WAIT_WARP(c, c.B.q_full, qi & 1);
       ++qi;
       g_cur = g;
       tc_fence_after();
     }
     for (int64_t t = t0; t < t1; ++t) {
       const int db = di & 1;
-      LVQ_WAIT_WARP(c.B.d_empty + db, ((di >> 1) & 1) ^ 1);
+      LVQ_WAIT_WARP(c, c.B.d_empty + db, ((di >> 1) & 1) ^ 1);
       tc_fence_after();
       const uint32_t d_tmem = c.tbase + db * N;
       for (int kb = 0; kb < a.n_kbox; ++kb) {
         const int s = ap.stage;
-        LVQ_WAIT_WARP(c.B.a_full + s, ap.phase);
+        LVQ_WAIT_WARP(c, c.B.a_full + s, ap.phase);
         tc_fence_after();
         const uint32_t a_tmem = c.tbase + 2 * N + s * kACols;
         // K step kk of this box reads query dims kg .. kg+15, kg = kb*box + 16kk:
@@ -345,7 +347,6 @@ out:
   if (elect_one()) mma_commit(c.B.mma_done);
   __syncwarp();
   (void)__all_sync(kFull, mbar_wait(c.B.mma_done, 0, kWaitLimit));
-#undef LVQ_WAIT_WARP
 }
 
 template <int N, int BITS>
@@ -363,7 +364,7 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
   cp.advance(parity, a.code_stages);
   ap.advance(parity, AS);
   int skip = parity;  // boxes to pass before this warp's next one
-  for (int64_t j = c.cta; j < a.jobs && !*c.abort_sh; j += c.grid) {
+  for (int64_t j = c.cta; j < a.jobs && !__any_sync(kFull, *c.abort_sh); j += c.grid) {
     const Job jb = job_of(a, j);
     const int64_t t0 = jb.t0, t1 = jb.t1;
     for (int64_t t = t0; t < t1; ++t) {
@@ -374,7 +375,7 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         }
         skip = 1;
         const int s = cp.stage;
-        LVQ_WAIT(c, c.B.code_full + s, cp.phase);
+        LVQ_WAIT_WARP(c, c.B.code_full + s, cp.phase);
         const uint4* src = reinterpret_cast<const uint4*>(c.cst + s * kStageBytes + row * kBoxBytes);
         uint4 w[4];
         const int sw = (row >> 1) & 3;  // 64-byte swizzle of the TMA box
@@ -383,7 +384,7 @@ __device__ __forceinline__ void unpack_role(const MmaArgs& a, const Ctx& c, int 
         __syncwarp();
         if (lane == 0) mbar_arrive(c.B.code_empty + s);
         const int as = ap.stage;
-        LVQ_WAIT(c, c.B.a_empty + as, ap.phase ^ 1);
+        LVQ_WAIT_WARP(c, c.B.a_empty + as, ap.phase ^ 1);
         tc_fence_after();
         const uint32_t taddr = lane_base + 2 * N + as * kACols;
         // tcgen05.st reads its source registers after issue: a register set
@@ -435,6 +436,9 @@ __device__ __forceinline__ RowMeta load_meta(const MmaArgs& a, int64_t rw, bool 
   r.neg_h = -0.5f * r.nrm;
   return r;
 }
+
+// Fetch the line holding p into L2 (a hint: no data returns).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // CM: how <q, mu_m> of the query tile is held in shared memory: 0 not at
 // all, 1 float16, 2 float32.
@@ -567,6 +571,20 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       tc_fence_after();
       const RowMeta cur = nxt;
       if (t + 1 < t1) nxt = load_meta(a, (t + 1) * kRows + row_in, ip);
+      // With up to 64 queries a tile takes only a few microseconds, and the
+      // codes stream from HBM: the per-row constants of the tile kMetaAhead
+      // tiles on are fetched into L2 now, so that the loads one tile ahead
+      // wait on L2 rather than HBM (one line per lane: 4 lines of each float
+      // array, the mean ids, the live words).
+      if (N <= 64 && et < 14 && t + kMetaAhead < t1) {
+        const int64_t r0 = (t + kMetaAhead) * kRows + (et & 3) * 32;
+        const int64_t r = r0 < a.n_rows ? r0 : a.n_rows - 1;
+        if (et < 4) prefetch_l2(st.lower + r);
+        else if (et < 8) prefetch_l2(st.step + r);
+        else if (et < 12) { if (!ip) prefetch_l2(st.norm2 + r); }
+        else if (et == 12) prefetch_l2(st.mean_id + r);
+        else prefetch_l2(st.live + (r >> 5));
+      }
       const int64_t rw = t * kRows + row_in;
       const float* cm_row = a.p.cm + q0 * st.n_means + cur.m;
       const __half* cm16_row = c.cm16 + cur.m;
@@ -718,7 +736,7 @@ __device__ __forceinline__ void bound_role(const MmaArgs& a, const Ctx& c, int l
   }
 }
 
-#undef LVQ_WAIT
+#undef LVQ_WAIT_WARP
 
 template <int N, int BITS, int CM>
 __global__ void __launch_bounds__(warps_of<N>() * 32, 1)
@@ -778,7 +796,7 @@ __global__ void __launch_bounds__(warps_of<N>() * 32, 1)
   c.tbase = *tmem_base_sh;
 
   if (warp == 0) {
-    if (lane == 0) producer_role<N, BITS>(&cmap, &qmap, a, c);
+    producer_role<N, BITS>(&cmap, &qmap, a, c, lane);
   } else if (warp == 1) {
     mma_role<N, BITS>(a, c, lane);
   } else if (warp < kEpiWarp0) {
