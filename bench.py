@@ -45,7 +45,7 @@ METRIC = "LVQ-4x8 distances/s & QPS@recall10 at 10M x 768"
 UNIT = "distances/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one scan_mma launch over
 # 2M rows with the bench's 12,716-query mix (ncu --set full, B300)
-SCAN_MMA_DRAM_BYTES_2M = 2.05227e9 + 0.827707e9
+SCAN_MMA_DRAM_BYTES_2M = 2.029857e9 + 0.817906e9
 # DRAM bytes (read + write) of one ID-gather launch of 1,024 queries x 2,048
 # candidate ids, from an ncu capture of the same launch size at 2M rows (the
 # launch's traffic depends on the candidates, not on the rows)

@@ -14,9 +14,11 @@
 //   warp 0      TMA producer: the CTA's query tile (N queries x all dims,
 //               float16, 128-byte swizzle, resident while the CTA works on
 //               that tile) and 128-row x 64-byte boxes of codes (64-byte
-//               swizzle) into a 3-stage ring;
+//               swizzle) into a ring of 3 to 16 stages;
 //   warp 1      allocates TMEM and issues tcgen05.mma (M = 128 database
 //               rows, N queries, K = 16) with A read from TMEM;
+//               both run as whole warps: every lane waits on the
+//               mbarriers, one elected lane issues;
 //   warps 2-9   unpack, two per TMEM lane quarter taking alternate code
 //               boxes (one box's tcgen05.st completes while the other's
 //               codes are read and converted): each thread owns one
