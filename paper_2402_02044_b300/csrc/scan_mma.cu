@@ -82,6 +82,10 @@ constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr int kMinSmem = 120 * 1024;    // keeps one CTA per SM (TMEM is taken whole)
 constexpr int kHistInts = 64;           // 6-bit-digit radix histogram of one warp
+// epilogue warps that cut candidate buffers: all eight with query tiles of up
+// to 64 (whose CTAs start with loose bounds and cut often), four with 128
+// (whose shared memory has no room for more histograms)
+__host__ __device__ constexpr int compact_warps(int n) { return n <= 64 ? 8 : 4; }
 constexpr int kMetaAhead = 4;           // tiles between the L2 prefetch of row constants and their use
 
 struct MmaArgs {
@@ -120,12 +124,12 @@ struct Smem {
 // (fewer registers held across its loop); the query tile (1024-byte
 // aligned for its swizzle) and the code stages follow.
 //   misc: tmem base, abort, verdicts (32 B) + thr[n] u64 + fq[n] float4 +
-//         qnorm[n] + cmabs[n] + hist[4][kHistInts]; then the mbarriers
+//         qnorm[n] + cmabs[n] + hist[compact_warps(n)][kHistInts]; then the mbarriers
 //         (64 x 8 B) and <q, mu_m> of the tile (cm_bytes, when held)
 __host__ __device__ inline Smem smem_layout(int n, int qboxes, int stages, int cm_bytes) {
   Smem s;
   s.misc = 0;
-  s.bars = 32 + n * 8 + n * 16 + n * 4 * 2 + 4 * kHistInts * 4;
+  s.bars = 32 + n * 8 + n * 16 + n * 4 * 2 + compact_warps(n) * kHistInts * 4;
   s.cm = s.bars + 64 * 8;
   s.q = (s.cm + cm_bytes + 1023) / 1024 * 1024;
   s.code = s.q + qboxes * n * 128;
@@ -218,7 +222,7 @@ struct Ctx {
                     //     filter value plus <q, mu_m> exceeds bound; count = keys buffered
   float* qnorm_s;
   float* cmabs_s;   // [N] max_m |<q, mu_m>|
-  int* hist;        // [4][kHistInts] radix histograms of the compacting warps
+  int* hist;        // [compact_warps(N)][kHistInts] radix histograms of the compacting warps
   __half* cm16;     // [N][M] <q, mu_m> in float16, or null
   float* cm32;      // [N][M] <q, mu_m> in float32, or null
   volatile int* ep_go;  // [2] epilogue leader's verdicts, read by the 4 epilogue warps after a named barrier
@@ -505,7 +509,8 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
   const DeviceStore& st = a.st;
   const bool ip = st.metric == LVQ_IP;
   uint64_t* mybuf = a.cand + (int64_t)c.cta * N * a.cap;
-  int* myhist = c.hist + (ew & 3) * kHistInts;  // used by warps 0-3
+  constexpr int kCW = compact_warps(N);
+  int* myhist = c.hist + (ew & (kCW - 1)) * kHistInts;  // used by warps 0 .. kCW-1
   uint32_t di = 0, pub = 0;
   // The eight epilogue warps meet at named barriers, so they must all take
   // the same path: only the first waits on mbarriers and reads the abort
@@ -656,14 +661,14 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       if (lane == 0) mbar_arrive(c.B.d_empty + db);
       ++di;
       named_bar(1, kEpiThreads);
-      if (ew < 4) {
-        // warps 0-3 compact the buffers that may not take another tile: warp
-        // ew owns queries ew, ew + 4, ... (one per lane, N <= 128), and only
+      if (ew < kCW) {
+        // warps 0 .. kCW-1 compact the buffers that may not take another
+        // tile: warp ew owns queries ew, ew + kCW, ... (one per lane), and only
         // those whose buffer is full are visited
-        const int nl = ew + 4 * lane;
+        const int nl = ew + kCW * lane;
         uint32_t full = __ballot_sync(kFull, nl < N && __float_as_int(c.fq[nl < N ? nl : 0].w) > a.cap - kRows);
         while (full) {
-          const int n = ew + 4 * (__ffs((int)full) - 1);
+          const int n = ew + kCW * (__ffs((int)full) - 1);
           full &= full - 1;
           const int cnt = __float_as_int(c.fq[n].w);
           {
@@ -684,10 +689,10 @@ __device__ __forceinline__ void epilogue_role(const MmaArgs& a, const Ctx& c, in
       }
       named_bar(1, kEpiThreads);
     }
-    if (ew < 4) {
+    if (ew < kCW) {
       // end of job: the k1 best of each query in segment jb.s; its k1-th key
       // bounds every job, and only keys at or below the bound are kept
-      for (int n = ew; n < N; n += 4) {
+      for (int n = ew; n < N; n += kCW) {
         if (q0 + n >= a.nq) continue;
         uint64_t tk;
         uint64_t* b0 = mybuf + n * a.cap;
