@@ -130,7 +130,9 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       : "memory");
 }
 // One lane of a converged warp (elect.sync): the issuing lane for tcgen05.mma
-// and tcgen05.commit when the whole warp runs the issuing loop.
+// and tcgen05.commit when the whole warp runs the issuing loop.  With the
+// full mask and all 32 lanes active the choice is the same every time, so a
+// commit tracks the MMAs that the same lane issued before it.
 __device__ __forceinline__ bool elect_one() {
   uint32_t pred = 0;
   asm volatile(
